@@ -1,0 +1,400 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 relativistic SHASTA solver.
+
+Workload: a 200^3 event of Gaussian hot spots (30 spots, centres in the
+central half of the box, sigma 3-8 cells, amplitudes log-uniform in [0.1, 10]
+on a 1e-6 background, n = e^(3/4), v = 0), ideal gas p = e/3, lambda = 0.4,
+reflecting walls, FP32 state.  One benchmark step is one full x/y/z split
+SHASTA step (three fused sweep kernels) of that state, resident in HBM.
+
+Prints one JSON line (rank 0).  value = cell-updates per second of the whole
+job (N replicas under torchrun: each rank advances its own event; there is
+no data-path collective, scaling is weak).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 oracle (the plain C reference the tests
+check the CUDA path against) on the host cores, on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s per 3D SHASTA step (FP32 vs FP64); served events/s + p99 latency"
+UNIT = "cell-updates/s"
+N_GRID = 200
+EVENT_STEPS = 200  # steps of one event of this workload (end-to-end leg)
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "mixed", "fp64"], default="fp32")
+    ap.add_argument("--grid", type=int, default=N_GRID)
+    ap.add_argument("--e2e-events", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-path", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(args):
+    return {
+        "workload": f"hot_spots_{args.grid}^3",
+        "grid": [args.grid] * 3,
+        "precision": args.precision,
+        "eos": "ideal p=e/3",
+        "bc": "reflect",
+        "lambda": 0.4,
+        "eta": 0.125,
+        "hot_spots": 30,
+        "seed": 2,
+        "event_steps": EVENT_STEPS,
+        "l2": "working set (2 buffers x 5 fields) above the 129 MB L2; no flush",
+        "data": "synthetic",
+    }
+
+
+def workload_prims(N, seed=2):
+    from paper_1206_0919_gb300 import workloads as W
+    return W.hot_spots(N=N, seed=seed, n_spots=30)
+
+
+# ------------------------------------------------------------- helpers ----
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("sweep.cuh", "sweep_f32.cu", "sweep_mixed.cu", "sweep_f64.cu"):
+        with open(os.path.join(ROOT, "paper_1206_0919_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(precision, grid):
+    """DRAM bytes per sweep launch from the committed ncu summary, if it was
+    taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "sweep_kernel_hot_spots.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    src = re.search(r"kernel sources sha256\[:16\]:\s*([0-9a-f]{16})", text)
+    if not src or src.group(1) != kernel_source_hash():
+        return None
+    m = re.search(rf"traffic_per_launch\[{precision},{grid}\]:\s*([0-9.eE+]+)", text)
+    return float(m.group(1)) if m else None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.device), "-lms", "100"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+            time.sleep(0.5)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.tmp.flush()
+
+    def summary(self, t0, t1):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.tmp.name) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                    frac = float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+                    rows.append((ts + frac, float(parts[2]), float(parts[3]), parts[5:9]))
+                except (ValueError, IndexError):
+                    continue
+        os.unlink(self.tmp.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        under = [r for r in rows if t0 - 0.15 <= r[0] <= t1 + 0.15] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in under for i, v in enumerate(r[3]) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[1] for r in under),
+                "sm_max_mhz": max(r[2] for r in under), "reasons": reasons,
+                "samples": len(under)}
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+# ---------------------------------------------------------- CPU oracle ----
+
+def oracle_rate(N, max_steps=3, target_s=10.0, threads=None):
+    """Oracle (FP64 C reference) cell-updates/s on the host cores."""
+    from oracle import oracle as OR
+    O = OR.default()
+    threads = threads or (os.cpu_count() or 1)
+    O.set_threads(threads)
+    P = OR.params((N, N, N))
+    U = O.prim2cons(P, *workload_prims(N).as_list())
+    steps, t_total = 0, 0.0
+    while steps < max_steps and (steps == 0 or t_total < target_s):
+        t = time.perf_counter()
+        U = O.step(P, U, 1, step0=steps)
+        t_total += time.perf_counter() - t
+        steps += 1
+    return N ** 3 * steps / t_total, threads, steps, t_total
+
+
+def _crop(prims, side):
+    """Centred side^3 crop of the workload's primitive fields."""
+    N = prims.e.shape[0]
+    lo = (N - side) // 2
+    sl = (slice(lo, lo + side),) * 3
+    return [a[sl].copy() for a in prims.as_list()]
+
+
+def run_reference(args):
+    """Oracle arm: each step is one full oracle step of a centred crop of the
+    workload, the crop sized so that warmup + steps take about two minutes."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    N = args.grid
+    from oracle import oracle as OR
+    O = OR.default()
+    threads = os.cpu_count() or 1
+    O.set_threads(threads)
+    prims = workload_prims(N)
+    probe = min(48, N)
+    Pp = OR.params((probe,) * 3)
+    Up = O.prim2cons(Pp, *_crop(prims, probe))
+    t = time.perf_counter()
+    O.step(Pp, Up, 1)
+    rate = probe ** 3 / (time.perf_counter() - t)
+    budget = 120.0 * rate / max(1, args.steps + args.warmup)
+    side = int(max(16, min(N, round(budget ** (1.0 / 3.0)))))
+    P = OR.params((side,) * 3)
+    U = O.prim2cons(P, *_crop(prims, side))
+    for w in range(args.warmup):
+        U = O.step(P, U, 1, step0=w)
+    t0 = time.perf_counter()
+    U = O.step(P, U, args.steps, step0=args.warmup)
+    dt = time.perf_counter() - t0
+    value = side ** 3 * args.steps / dt
+    sample = (f"{args.steps} full oracle steps of the centred {side}^3 crop of the {N}^3 state "
+              f"({dt:.1f} s)")
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(args),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- ours ----
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1206_0919_gb300 import shasta as S
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device (no CPU fallback exists)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    N = args.grid
+    ncell = N ** 3
+    prims = workload_prims(N, seed=2 + 1000 * rank)
+    stream = torch.cuda.Stream()
+    solver = S.Solver((N, N, N), precision=args.precision, stream=stream.cuda_stream,
+                      device=local)
+    solver.set_primitives(*prims.as_list())
+    solver.step(args.warmup)
+    solver.sync()
+
+    # timed region: K steps, events between steps on the solver's stream
+    sampler = ClockSampler(local)
+    sampler.start()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    evs[0].record(stream)
+    for k in range(args.steps):
+        solver.step(1)
+        evs[k + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t_wall1 = time.time()
+    sampler.stop()
+    clocks = sampler.summary(t_wall0, t_wall1)
+    ms = evs[0].elapsed_time(evs[-1])
+    step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * ncell * args.steps / (ms / 1e3)
+
+    # roofline of the sweep kernel (the only kernel of a step: 3 launches)
+    word = 8 if args.precision == "fp64" else 4
+    bytes_per_launch = ncell * 5 * word * 2  # read + write of the five conserved fields
+    launch_s = (ms / 1e3) / (3 * args.steps)
+    achieved = bytes_per_launch / launch_s / 1e9
+    peak, peak_kind = measured_peak()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": committed_traffic(args.precision, N),
+                "kernel": f"sweep_kernel ({args.precision})",
+                "algorithmic_bytes_per_launch": bytes_per_launch}
+
+    # per-axis sweep durations (after the timed region)
+    per_axis = {}
+    for ax in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(10):
+            solver.sweep(ax)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_ax = e0.elapsed_time(e1) / 10
+        per_axis["xyz"[ax]] = {"ms": t_ax, "GB/s": bytes_per_launch / (t_ax / 1e3) / 1e9}
+
+    # end-to-end: one event through the public API with pinned host buffers
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    host_in = [pin(a) for a in prims.as_list()]
+    host_out = [torch.empty(prims.e.shape, dtype=torch.float64).pin_memory().numpy()
+                for _ in range(6)]
+    solver.set_primitives(*host_in)
+    solver.step(2)
+    solver.get_primitives(host_out)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_events):
+        solver.set_primitives(*host_in)
+        solver.step(EVENT_STEPS)
+        solver.get_primitives(host_out)
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * ncell * EVENT_STEPS * args.e2e_events / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": 5 * 8 * ncell, "d2h_bytes_per_step": 6 * 8 * ncell,
+           "step": f"one event: set_primitives from pinned host, {EVENT_STEPS} steps, "
+                   "get_primitives to pinned host"}
+
+    extra = {}
+    if not args.no_fp64_path and args.precision != "fp64":
+        # the plain FP64 single-event GPU path on the same workload
+        with S.Solver((N, N, N), precision="fp64", stream=stream.cuda_stream, device=local) as s64:
+            s64.set_primitives(*prims.as_list())
+            s64.step(3)
+            s64.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            k64 = 10
+            e0.record(stream)
+            s64.step(k64)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            r64 = ncell * k64 / (e0.elapsed_time(e1) / 1e3)
+        extra["fp64_path"] = {"value": r64, "unit": UNIT,
+                              "speedup_of_value": value / world / r64}
+    solver.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, threads, steps, t = oracle_rate(N)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{steps} full oracle step(s) of the {N}^3 state ({t:.1f} s)"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "mixed": "f32+f64", "fp64": "f64"}[args.precision],
+            "data": "synthetic", "config": workload_config(args),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": 3 * args.steps, "clocks": clocks,
+            "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms),
+                        "max": max(step_ms)},
+            "per_axis_sweep": per_axis,
+        }
+        out.update(extra)
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,186 @@
+/*
+ * shasta.h -- C ABI of a GB300-native relativistic SHASTA solver.
+ *
+ * The solver advances the conserved energy E, momentum (Mx, My, Mz) and
+ * baryon density R of ideal relativistic hydrodynamics on a Cartesian grid
+ * (J. Gerhard, V. Lindenstruth, M. Bleicher, "Relativistic Hydrodynamics on
+ * Graphic Cards", arXiv:1206.0919).  Sec. 2 defines the system: the
+ * conservation laws of T^{mu nu} and of the baryon current, with
+ *   R = n gamma, M = (e + p) gamma^2 v, E = (e + p v^2) gamma^2.
+ * Sec. 3 defines one time step: dimensionally split sweeps, each a half step
+ * and a full step of geometric transport with pressure sources, phoenical
+ * antidiffusion and the flux limiter, followed by the recovery of the
+ * primitive variables (e, v, n, p) through the equation of state.
+ *
+ * Conventions shared by every call:
+ *  - Arrays are dense nx*ny*nz grids with x fastest, element (i, j, k) at
+ *    index i + nx*(j + ny*k).  They are always double precision at the ABI,
+ *    whatever the precision the solver keeps its state in.
+ *  - mem = SHASTA_MEM_HOST: ordinary host pointers (pinned memory makes the
+ *    copies asynchronous-capable and faster).  SHASTA_MEM_DEVICE: device
+ *    pointers on the context's device.  Arrays passed in are copied; the
+ *    caller keeps ownership of every pointer it passes.
+ *  - Every call returns a shasta_status.  No call throws or aborts; after an
+ *    error, shasta_last_error(ctx) holds a one-line message.  A context may
+ *    be used by one host thread at a time.
+ *  - The library owns its device state.  Work is enqueued on the context's
+ *    stream; calls that return data to the host synchronise that stream.
+ */
+#ifndef SHASTA_H
+#define SHASTA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum shasta_status {
+  SHASTA_OK = 0,
+  SHASTA_EINVAL = 1,      /* bad argument (sizes, pointers, parameters) */
+  SHASTA_ENOMEM = 2,      /* device or host allocation failed */
+  SHASTA_EAGAIN = 3,      /* try again later (queue full, result not ready) */
+  SHASTA_EUNPHYSICAL = 4, /* input state with non-finite values, E < 0 or |M| >= E */
+  SHASTA_ETIMEOUT = 5,    /* a bounded wait ran out */
+  SHASTA_ECUDA = 6,       /* a CUDA runtime call failed (message in last_error) */
+  SHASTA_ENOTFOUND = 7    /* unknown ticket or handle */
+} shasta_status;
+
+/* Boundary rule at the six faces (Sec. 3.1.3 keeps halo cells around the
+ * grid).  REFLECT: mirror image through the wall, the momentum normal to it
+ * negated.  PERIODIC: wrap.  FROZEN: three ghost layers per face hold the
+ * edge cell of the state given to the last set call and never change (the
+ * paper's halo cells copied through unchanged). */
+enum { SHASTA_BC_REFLECT = 0, SHASTA_BC_PERIODIC = 1, SHASTA_BC_FROZEN = 2 };
+
+/* Equation of state.  IDEAL: p = e/3 (Sec. 2).  BAG: p = e/3 for e <= e_c and
+ * p = (e - 4B)/3 above (not in the paper; requires 0 <= 4B <= e_c). */
+enum { SHASTA_EOS_IDEAL = 0, SHASTA_EOS_BAG = 1 };
+
+/* Precision of the device state and arithmetic.  FP64: everything in double.
+ * FP32: state, transport, limiter and recovery in float.  MIXED: state,
+ * transport and limiter in float; the recovery of the primitives (where
+ * 1 - v^2 cancels as v -> 1, Sec. 4-5) in double. */
+enum { SHASTA_FP64 = 0, SHASTA_FP32 = 1, SHASTA_MIXED = 2 };
+
+enum { SHASTA_MEM_HOST = 0, SHASTA_MEM_DEVICE = 1 };
+
+typedef struct shasta_grid {
+  int nx, ny, nz; /* interior cells per axis, each >= 1 */
+  int bc;         /* SHASTA_BC_* */
+} shasta_grid;
+
+typedef struct shasta_eos {
+  int kind;   /* SHASTA_EOS_* */
+  double B;   /* bag constant (BAG only) */
+  double e_c; /* branch point of the bag EoS (BAG only) */
+} shasta_eos;
+
+typedef struct shasta_opts {
+  int precision; /* SHASTA_FP64 / SHASTA_FP32 / SHASTA_MIXED */
+  double eta;    /* outer antidiffusion coefficient; Sec. 3 uses 1/8 */
+  double delta;  /* recovery clamps |M| to (1 - delta) E; 0 selects 1e-10 (FP64)
+                    or 1e-6 (FP32, MIXED) */
+  void* stream;  /* cudaStream_t to enqueue on; NULL: the context makes its own */
+  int device;    /* CUDA device ordinal */
+  int check_input; /* nonzero: set calls scan the state and return
+                      SHASTA_EUNPHYSICAL for non-finite values, E < 0 or |M| >= E */
+} shasta_opts;
+
+typedef struct shasta_ctx shasta_ctx;
+
+/* Fills *o with the defaults: FP32, eta = 1/8, delta = 0, stream NULL,
+ * device 0, check_input 1. */
+void shasta_default_opts(shasta_opts* o);
+
+/* Creates a solver for one event.  dx is the cell size, lambda = dt/dx the
+ * CFL number of Sec. 3 (0 < lambda <= 0.5); the time step is dt = lambda*dx.
+ * eos may be NULL (ideal gas), o may be NULL (defaults).  Allocates two
+ * copies of the five conserved fields on the device (double buffering,
+ * Sec. 3.1.3).  Errors: EINVAL (sizes < 1, bad lambda/eta/eos, NULL out),
+ * ENOMEM, ECUDA.  On error *out is NULL and shasta_last_error(NULL) holds
+ * the message. */
+shasta_status shasta_create(const shasta_grid* g, double dx, double lambda,
+                            const shasta_eos* eos, const shasta_opts* o, shasta_ctx** out);
+
+/* Releases every resource of ctx (NULL is accepted).  Synchronises first. */
+shasta_status shasta_destroy(shasta_ctx* ctx);
+
+/* Sets the conserved state (Sec. 2, Eqs. cf-density, cf-momentum,
+ * cf-energy).  Five arrays of nx*ny*nz doubles in memory space mem.  Resets
+ * the step counter to 0.  Errors: EINVAL (NULL pointer or bad mem),
+ * EUNPHYSICAL (check_input set and the state is not physical), ECUDA. */
+shasta_status shasta_set_conserved(shasta_ctx* ctx, const double* E, const double* Mx,
+                                   const double* My, const double* Mz, const double* R,
+                                   int mem);
+
+/* Sets the state from primitives: rest-frame energy density e, velocity v,
+ * baryon density n (Sec. 2 map to E, M, R, computed on the device).  Same
+ * layout, ownership and errors as shasta_set_conserved (|v| >= 1 or e < 0
+ * gives EUNPHYSICAL when check_input is set). */
+shasta_status shasta_set_primitives(shasta_ctx* ctx, const double* e, const double* vx,
+                                    const double* vy, const double* vz, const double* n,
+                                    int mem);
+
+/* Enqueues nsteps full split steps (nsteps >= 0) and returns without
+ * waiting.  Step k sweeps the axes in the order of entries 3(k mod 6) ..
+ * 3(k mod 6)+2 of the permutation table of Sec. 3.1.4
+ * {x,y,z, x,z,y, z,x,y, z,y,x, y,z,x, y,x,z}.  Each sweep is one fused
+ * kernel: recovery at level n, half step (lambda/2), recovery at n+1/2,
+ * full step from the old state (Sec. 3).  Errors: EINVAL (state never set,
+ * nsteps < 0), ECUDA. */
+shasta_status shasta_step(shasta_ctx* ctx, int nsteps);
+
+/* Enqueues ONE sweep along axis (0 = x, 1 = y, 2 = z): the fused kernel of
+ * shasta_step for a single axis.  Does not change the step counter; used to
+ * time or study one sweep.  Errors: EINVAL (bad axis, state never set), ECUDA. */
+shasta_status shasta_sweep(shasta_ctx* ctx, int axis);
+
+/* Waits until all work enqueued on the context's stream has finished. */
+shasta_status shasta_sync(shasta_ctx* ctx);
+
+/* Copies the conserved state out (five arrays, any may be NULL to skip).
+ * Synchronous with respect to the context's stream. */
+shasta_status shasta_get_conserved(shasta_ctx* ctx, double* E, double* Mx, double* My,
+                                   double* Mz, double* R, int mem);
+
+/* Recovers and copies out the primitives e, vx, vy, vz, n, p of the current
+ * state (Sec. 3 phases 3-4; any pointer may be NULL to skip).  Synchronous. */
+shasta_status shasta_get_primitives(shasta_ctx* ctx, double* e, double* vx, double* vy,
+                                    double* vz, double* n, double* p, int mem);
+
+/* Sums of E, Mx, My, Mz, R over the grid, accumulated in double on the
+ * device with a fixed reduction order (deterministic).  out: 5 host doubles.
+ * Synchronous. */
+shasta_status shasta_totals(shasta_ctx* ctx, double out[5]);
+
+/* Number of full steps taken since the state was last set (the permutation
+ * phase is this mod 6). */
+int64_t shasta_steps_done(const shasta_ctx* ctx);
+
+/* Sets the step counter, e.g. to resume from a checkpoint taken with
+ * shasta_get_conserved + shasta_steps_done.  Errors: EINVAL (negative). */
+shasta_status shasta_set_step_counter(shasta_ctx* ctx, int64_t steps);
+
+/* Device counters since the state was last set: out[0] = cell recoveries in
+ * which |M| was clamped or E <= 0 (the solver's vacuum/clamp reading).
+ * Synchronous. */
+shasta_status shasta_counters(shasta_ctx* ctx, int64_t out[1]);
+
+/* The context's stream (cudaStream_t as void*). */
+void* shasta_stream(const shasta_ctx* ctx);
+
+/* Last error message of ctx, or of the calling thread's last failed create
+ * when ctx is NULL.  Never NULL; "" when there was no error. */
+const char* shasta_last_error(const shasta_ctx* ctx);
+
+/* Name of a status code. */
+const char* shasta_status_string(shasta_status s);
+
+/* Library version string. */
+const char* shasta_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SHASTA_H */

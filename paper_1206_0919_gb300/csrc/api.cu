@@ -1,0 +1,512 @@
+// api.cu -- the C ABI of include/shasta.h: contexts, state transfer and the
+// step loop.  Every numerical step runs in the kernels of this library.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "../../include/shasta.h"
+#include "kernels.h"
+
+using namespace shasta;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+const char* kVersion = "shasta-gb300 0.1 (sm_103a)";
+
+// Fixed permutation of the sweep axes, Sec. 3.1.4.
+const int kAxisTable[18] = {0, 1, 2, 0, 2, 1, 2, 0, 1, 2, 1, 0, 1, 2, 0, 1, 0, 2};
+
+}  // namespace
+
+struct shasta_ctx {
+  int device = 0;
+  shasta_grid g{};
+  double dx = 1, lambda = 0.4;
+  shasta_eos eos{};
+  shasta_opts o{};
+  int is32 = 1;
+  size_t ncell = 0, esize = 4;
+  void* state_mem = nullptr;  // both buffers, 10 fields
+  void* buf[2][NF] = {};
+  int cur = 0;
+  bool state_set = false;
+  void* frozen = nullptr;
+  double* staging = nullptr;  // 6 * ncell doubles, allocated on first host transfer
+  double* partials = nullptr;
+  double* d_tot = nullptr;
+  unsigned long long* d_count = nullptr;  // [0] clamp count, [1] check scratch
+  double* h_small = nullptr;              // pinned: 5 totals + counters
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int64_t steps = 0;
+  std::string err;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int now = -1;
+    if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+  }
+};
+
+shasta_status fail(shasta_ctx* c, shasta_status s, const std::string& msg) {
+  if (c)
+    c->err = msg;
+  else
+    g_create_error = msg;
+  return s;
+}
+
+shasta_status cuda_fail(shasta_ctx* c, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return fail(c, e == cudaErrorMemoryAllocation ? SHASTA_ENOMEM : SHASTA_ECUDA, m);
+}
+
+#define CK(call, where)                                    \
+  do {                                                     \
+    cudaError_t _e = (call);                               \
+    if (_e != cudaSuccess) return cuda_fail(c, _e, where); \
+  } while (0)
+
+EosParams eos_params(const shasta_ctx* c) {
+  EosParams q;
+  q.kind = c->eos.kind;
+  q.B = c->eos.B;
+  q.ec = c->eos.e_c;
+  q.omd = 1.0 - c->o.delta;
+  return q;
+}
+
+shasta_status ensure_staging(shasta_ctx* c) {
+  if (c->staging) return SHASTA_OK;
+  CK(cudaMalloc((void**)&c->staging, 6 * c->ncell * sizeof(double)), "cudaMalloc staging");
+  return SHASTA_OK;
+}
+
+// Copies five caller arrays into device doubles: returns device pointers
+// (the caller's own for DEVICE memory, the staging area for HOST memory).
+shasta_status stage_in(shasta_ctx* c, const double* const src[5], int mem, const double* out[5]) {
+  if (mem == SHASTA_MEM_DEVICE) {
+    for (int k = 0; k < 5; ++k) out[k] = src[k];
+    return SHASTA_OK;
+  }
+  shasta_status s = ensure_staging(c);
+  if (s != SHASTA_OK) return s;
+  for (int k = 0; k < 5; ++k) {
+    double* d = c->staging + (size_t)k * c->ncell;
+    CK(cudaMemcpyAsync(d, src[k], c->ncell * sizeof(double), cudaMemcpyHostToDevice, c->stream),
+       "cudaMemcpyAsync H2D");
+    out[k] = d;
+  }
+  return SHASTA_OK;
+}
+
+shasta_status check_count(shasta_ctx* c, bool prims, const double* const f[5]) {
+  CK(cudaMemsetAsync(c->d_count + 1, 0, sizeof(unsigned long long), c->stream), "memset");
+  if (prims)
+    CK(launch_check_prims(f, c->ncell, c->d_count + 1, c->stream), "check_prims");
+  else
+    CK(launch_check_cons(f, c->ncell, c->d_count + 1, c->stream), "check_cons");
+  unsigned long long* h = reinterpret_cast<unsigned long long*>(c->h_small + 8);
+  CK(cudaMemcpyAsync(h, c->d_count + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                     c->stream),
+     "memcpy count");
+  CK(cudaStreamSynchronize(c->stream), "sync");
+  if (*h) {
+    char m[160];
+    snprintf(m, sizeof m, "%llu cells are not physical (non-finite, %s)", *h,
+             prims ? "e < 0, n < 0 or |v| >= 1" : "E < 0 or |M| >= E");
+    return fail(c, SHASTA_EUNPHYSICAL, m);
+  }
+  return SHASTA_OK;
+}
+
+shasta_status after_set(shasta_ctx* c) {
+  if (c->g.bc == SHASTA_BC_FROZEN) {
+    const void* f[5];
+    for (int k = 0; k < 5; ++k) f[k] = c->buf[c->cur][k];
+    CK(launch_frozen_capture(f, c->frozen, c->g.nx, c->g.ny, c->g.nz, c->is32, c->stream),
+       "frozen_capture");
+  }
+  CK(cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), c->stream), "memset");
+  c->state_set = true;
+  c->steps = 0;
+  return SHASTA_OK;
+}
+
+SweepParams sweep_params(shasta_ctx* c, int axis, int from) {
+  SweepParams P;
+  memset(&P, 0, sizeof P);
+  long long nx = c->g.nx, ny = c->g.ny, nz = c->g.nz;
+  for (int k = 0; k < NF; ++k) {
+    P.in[k] = c->buf[from][k];
+    P.out[k] = c->buf[from ^ 1][k];
+  }
+  if (axis == 0) {
+    P.n = (int)nx;
+    P.stride = 1;
+    P.plane = ny * nz;
+    P.nb = (int)ny;
+    P.sb = nx;
+    P.sc = nx * ny;
+  } else if (axis == 1) {
+    P.n = (int)ny;
+    P.stride = nx;
+    P.plane = nx * nz;
+    P.nb = (int)nx;
+    P.sb = 1;
+    P.sc = nx * ny;
+  } else {
+    P.n = (int)nz;
+    P.stride = nx * ny;
+    P.plane = nx * ny;
+    P.nb = (int)nx;
+    P.sb = 1;
+    P.sc = nx;
+  }
+  P.bc = c->g.bc;
+  P.frozen = c->frozen ? (const char*)c->frozen +
+                             frozen_axis_offset((int)nx, (int)ny, (int)nz, axis) * c->esize
+                       : nullptr;
+  P.tau_h = 0.5 * c->lambda;
+  P.tau_f = c->lambda;
+  P.htau_h = 0.5 * P.tau_h;
+  P.htau_f = 0.5 * P.tau_f;
+  P.eta = c->o.eta;
+  P.omd = 1.0 - c->o.delta;
+  P.bag_B = c->eos.B;
+  P.bag_ec = c->eos.e_c;
+  P.clamp_count = c->d_count;
+  return P;
+}
+
+cudaError_t launch_sweep(shasta_ctx* c, int axis) {
+  SweepParams P = sweep_params(c, axis, c->cur);
+  cudaError_t e;
+  if (c->o.precision == SHASTA_FP64)
+    e = launch_sweep_f64(P, axis, c->eos.kind, c->stream);
+  else if (c->o.precision == SHASTA_MIXED)
+    e = launch_sweep_mixed(P, axis, c->eos.kind, c->stream);
+  else
+    e = launch_sweep_f32(P, axis, c->eos.kind, c->stream);
+  if (e == cudaSuccess) c->cur ^= 1;
+  return e;
+}
+
+void release(shasta_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  cudaFree(c->state_mem);
+  cudaFree(c->frozen);
+  cudaFree(c->staging);
+  cudaFree(c->partials);
+  cudaFree(c->d_tot);
+  cudaFree(c->d_count);
+  cudaFreeHost(c->h_small);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+}  // namespace
+
+extern "C" {
+
+void shasta_default_opts(shasta_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->precision = SHASTA_FP32;
+  o->eta = 0.125;
+  o->delta = 0.0;
+  o->stream = nullptr;
+  o->device = 0;
+  o->check_input = 1;
+}
+
+shasta_status shasta_create(const shasta_grid* g, double dx, double lambda, const shasta_eos* eos,
+                            const shasta_opts* o, shasta_ctx** out) {
+  g_create_error.clear();
+  if (!out) return fail(nullptr, SHASTA_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!g) return fail(nullptr, SHASTA_EINVAL, "grid is NULL");
+  if (g->nx < 1 || g->ny < 1 || g->nz < 1)
+    return fail(nullptr, SHASTA_EINVAL, "grid sizes must be >= 1");
+  if ((long long)g->nx * g->ny > (1LL << 31) || (long long)g->ny * g->nz > (1LL << 31) ||
+      (long long)g->nx * g->nz > (1LL << 31))
+    return fail(nullptr, SHASTA_EINVAL, "grid plane too large");
+  if (g->bc < SHASTA_BC_REFLECT || g->bc > SHASTA_BC_FROZEN)
+    return fail(nullptr, SHASTA_EINVAL, "unknown boundary rule");
+  if (!(dx > 0) || !isfinite(dx)) return fail(nullptr, SHASTA_EINVAL, "dx must be > 0");
+  if (!(lambda > 0.0 && lambda <= 0.5)) return fail(nullptr, SHASTA_EINVAL, "need 0 < lambda <= 0.5");
+  shasta_opts opts;
+  if (o)
+    opts = *o;
+  else
+    shasta_default_opts(&opts);
+  if (opts.precision < SHASTA_FP64 || opts.precision > SHASTA_MIXED)
+    return fail(nullptr, SHASTA_EINVAL, "unknown precision");
+  if (!(opts.eta >= 0.0 && opts.eta <= 0.5)) return fail(nullptr, SHASTA_EINVAL, "need 0 <= eta <= 0.5");
+  if (!(opts.delta >= 0.0 && opts.delta < 0.5)) return fail(nullptr, SHASTA_EINVAL, "need 0 <= delta < 0.5");
+  if (opts.delta == 0.0) opts.delta = opts.precision == SHASTA_FP64 ? 1e-10 : 1e-6;
+  shasta_eos e;
+  if (eos)
+    e = *eos;
+  else {
+    e.kind = SHASTA_EOS_IDEAL;
+    e.B = 0.0;
+    e.e_c = 0.0;
+  }
+  if (e.kind != SHASTA_EOS_IDEAL && e.kind != SHASTA_EOS_BAG)
+    return fail(nullptr, SHASTA_EINVAL, "unknown EoS");
+  if (e.kind == SHASTA_EOS_BAG && !(e.B >= 0.0 && 4.0 * e.B <= e.e_c))
+    return fail(nullptr, SHASTA_EINVAL, "bag EoS needs 0 <= 4B <= e_c");
+  int ndev = 0;
+  cudaError_t ce = cudaGetDeviceCount(&ndev);
+  if (ce != cudaSuccess || ndev < 1)
+    return fail(nullptr, SHASTA_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(ce));
+  if (opts.device < 0 || opts.device >= ndev) return fail(nullptr, SHASTA_EINVAL, "bad device ordinal");
+
+  shasta_ctx* c = new (std::nothrow) shasta_ctx();
+  if (!c) return fail(nullptr, SHASTA_ENOMEM, "host allocation failed");
+  c->device = opts.device;
+  DeviceGuard dg(c->device);
+  c->g = *g;
+  c->dx = dx;
+  c->lambda = lambda;
+  c->eos = e;
+  c->o = opts;
+  c->is32 = opts.precision != SHASTA_FP64;
+  c->esize = c->is32 ? 4 : 8;
+  c->ncell = (size_t)g->nx * g->ny * g->nz;
+  auto bail = [&](cudaError_t err, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(err);
+    release(c);
+    return fail(nullptr, err == cudaErrorMemoryAllocation ? SHASTA_ENOMEM : SHASTA_ECUDA, m);
+  };
+  // 10 fields, each padded to 256 bytes
+  size_t field_bytes = ((c->ncell * c->esize + 255) / 256) * 256;
+  cudaError_t err = cudaMalloc(&c->state_mem, 2 * NF * field_bytes);
+  if (err != cudaSuccess) return bail(err, "cudaMalloc state");
+  for (int b = 0; b < 2; ++b)
+    for (int k = 0; k < NF; ++k) c->buf[b][k] = (char*)c->state_mem + (b * NF + k) * field_bytes;
+  if (g->bc == SHASTA_BC_FROZEN) {
+    err = cudaMalloc(&c->frozen, frozen_elems(g->nx, g->ny, g->nz) * c->esize);
+    if (err != cudaSuccess) return bail(err, "cudaMalloc frozen");
+  }
+  err = cudaMalloc((void**)&c->partials, 5 * 1024 * sizeof(double));
+  if (err != cudaSuccess) return bail(err, "cudaMalloc partials");
+  err = cudaMalloc((void**)&c->d_tot, 8 * sizeof(double));
+  if (err != cudaSuccess) return bail(err, "cudaMalloc totals");
+  err = cudaMalloc((void**)&c->d_count, 4 * sizeof(unsigned long long));
+  if (err != cudaSuccess) return bail(err, "cudaMalloc counters");
+  err = cudaMemset(c->d_count, 0, 4 * sizeof(unsigned long long));
+  if (err != cudaSuccess) return bail(err, "cudaMemset counters");
+  err = cudaMallocHost((void**)&c->h_small, 16 * sizeof(double));
+  if (err != cudaSuccess) return bail(err, "cudaMallocHost");
+  if (opts.stream) {
+    c->stream = (cudaStream_t)opts.stream;
+  } else {
+    err = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (err != cudaSuccess) return bail(err, "cudaStreamCreate");
+    c->own_stream = true;
+  }
+  *out = c;
+  return SHASTA_OK;
+}
+
+shasta_status shasta_destroy(shasta_ctx* c) {
+  if (!c) return SHASTA_OK;
+  DeviceGuard dg(c->device);
+  release(c);
+  return SHASTA_OK;
+}
+
+shasta_status shasta_set_conserved(shasta_ctx* c, const double* E, const double* Mx,
+                                   const double* My, const double* Mz, const double* R, int mem) {
+  if (!c) return SHASTA_EINVAL;
+  if (!E || !Mx || !My || !Mz || !R) return fail(c, SHASTA_EINVAL, "NULL field pointer");
+  if (mem != SHASTA_MEM_HOST && mem != SHASTA_MEM_DEVICE) return fail(c, SHASTA_EINVAL, "bad mem");
+  DeviceGuard dg(c->device);
+  const double* src[5] = {E, Mx, My, Mz, R};
+  const double* d[5];
+  shasta_status s = stage_in(c, src, mem, d);
+  if (s != SHASTA_OK) return s;
+  if (c->o.check_input) {
+    s = check_count(c, false, d);
+    if (s != SHASTA_OK) return s;
+  }
+  c->cur = 0;
+  for (int k = 0; k < 5; ++k)
+    CK(launch_from_f64(d[k], c->buf[0][k], c->ncell, c->is32, c->stream), "convert in");
+  return after_set(c);
+}
+
+shasta_status shasta_set_primitives(shasta_ctx* c, const double* e, const double* vx,
+                                    const double* vy, const double* vz, const double* n, int mem) {
+  if (!c) return SHASTA_EINVAL;
+  if (!e || !vx || !vy || !vz || !n) return fail(c, SHASTA_EINVAL, "NULL field pointer");
+  if (mem != SHASTA_MEM_HOST && mem != SHASTA_MEM_DEVICE) return fail(c, SHASTA_EINVAL, "bad mem");
+  DeviceGuard dg(c->device);
+  const double* src[5] = {e, vx, vy, vz, n};
+  const double* d[5];
+  shasta_status s = stage_in(c, src, mem, d);
+  if (s != SHASTA_OK) return s;
+  if (c->o.check_input) {
+    s = check_count(c, true, d);
+    if (s != SHASTA_OK) return s;
+  }
+  c->cur = 0;
+  void* out[5];
+  for (int k = 0; k < 5; ++k) out[k] = c->buf[0][k];
+  CK(launch_prim2cons(d, out, c->ncell, c->is32, eos_params(c), c->stream), "prim2cons");
+  return after_set(c);
+}
+
+shasta_status shasta_step(shasta_ctx* c, int nsteps) {
+  if (!c) return SHASTA_EINVAL;
+  if (nsteps < 0) return fail(c, SHASTA_EINVAL, "nsteps < 0");
+  if (!c->state_set) return fail(c, SHASTA_EINVAL, "state not set");
+  DeviceGuard dg(c->device);
+  for (int s = 0; s < nsteps; ++s) {
+    int ph = (int)((c->steps) % 6);
+    for (int sub = 0; sub < 3; ++sub) CK(launch_sweep(c, kAxisTable[3 * ph + sub]), "sweep launch");
+    ++c->steps;
+  }
+  return SHASTA_OK;
+}
+
+shasta_status shasta_sweep(shasta_ctx* c, int axis) {
+  if (!c) return SHASTA_EINVAL;
+  if (axis < 0 || axis > 2) return fail(c, SHASTA_EINVAL, "axis must be 0, 1 or 2");
+  if (!c->state_set) return fail(c, SHASTA_EINVAL, "state not set");
+  DeviceGuard dg(c->device);
+  CK(launch_sweep(c, axis), "sweep launch");
+  return SHASTA_OK;
+}
+
+shasta_status shasta_sync(shasta_ctx* c) {
+  if (!c) return SHASTA_EINVAL;
+  DeviceGuard dg(c->device);
+  CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  return SHASTA_OK;
+}
+
+shasta_status shasta_get_conserved(shasta_ctx* c, double* E, double* Mx, double* My, double* Mz,
+                                   double* R, int mem) {
+  if (!c) return SHASTA_EINVAL;
+  if (mem != SHASTA_MEM_HOST && mem != SHASTA_MEM_DEVICE) return fail(c, SHASTA_EINVAL, "bad mem");
+  if (!c->state_set) return fail(c, SHASTA_EINVAL, "state not set");
+  DeviceGuard dg(c->device);
+  double* dst[5] = {E, Mx, My, Mz, R};
+  if (mem == SHASTA_MEM_HOST) {
+    shasta_status s = ensure_staging(c);
+    if (s != SHASTA_OK) return s;
+  }
+  for (int k = 0; k < 5; ++k) {
+    if (!dst[k]) continue;
+    double* d = mem == SHASTA_MEM_DEVICE ? dst[k] : c->staging + (size_t)k * c->ncell;
+    CK(launch_to_f64(c->buf[c->cur][k], d, c->ncell, c->is32, c->stream), "convert out");
+    if (mem == SHASTA_MEM_HOST)
+      CK(cudaMemcpyAsync(dst[k], d, c->ncell * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+         "cudaMemcpyAsync D2H");
+  }
+  CK(cudaStreamSynchronize(c->stream), "sync");
+  return SHASTA_OK;
+}
+
+shasta_status shasta_get_primitives(shasta_ctx* c, double* e, double* vx, double* vy, double* vz,
+                                    double* n, double* p, int mem) {
+  if (!c) return SHASTA_EINVAL;
+  if (mem != SHASTA_MEM_HOST && mem != SHASTA_MEM_DEVICE) return fail(c, SHASTA_EINVAL, "bad mem");
+  if (!c->state_set) return fail(c, SHASTA_EINVAL, "state not set");
+  DeviceGuard dg(c->device);
+  double* dst[6] = {e, vx, vy, vz, n, p};
+  double* d[6];
+  if (mem == SHASTA_MEM_HOST) {
+    shasta_status s = ensure_staging(c);
+    if (s != SHASTA_OK) return s;
+  }
+  for (int k = 0; k < 6; ++k)
+    d[k] = !dst[k] ? nullptr : (mem == SHASTA_MEM_DEVICE ? dst[k] : c->staging + (size_t)k * c->ncell);
+  const void* in[5];
+  for (int k = 0; k < 5; ++k) in[k] = c->buf[c->cur][k];
+  CK(launch_recover(in, d, c->ncell, c->is32, eos_params(c), c->stream), "recover");
+  if (mem == SHASTA_MEM_HOST)
+    for (int k = 0; k < 6; ++k)
+      if (dst[k])
+        CK(cudaMemcpyAsync(dst[k], d[k], c->ncell * sizeof(double), cudaMemcpyDeviceToHost,
+                           c->stream),
+           "cudaMemcpyAsync D2H");
+  CK(cudaStreamSynchronize(c->stream), "sync");
+  return SHASTA_OK;
+}
+
+shasta_status shasta_totals(shasta_ctx* c, double out[5]) {
+  if (!c || !out) return SHASTA_EINVAL;
+  if (!c->state_set) return fail(c, SHASTA_EINVAL, "state not set");
+  DeviceGuard dg(c->device);
+  const void* f[5];
+  for (int k = 0; k < 5; ++k) f[k] = c->buf[c->cur][k];
+  CK(launch_totals(f, c->ncell, c->is32, c->partials, c->d_tot, c->stream), "totals");
+  CK(cudaMemcpyAsync(c->h_small, c->d_tot, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+     "memcpy totals");
+  CK(cudaStreamSynchronize(c->stream), "sync");
+  for (int k = 0; k < 5; ++k) out[k] = c->h_small[k];
+  return SHASTA_OK;
+}
+
+int64_t shasta_steps_done(const shasta_ctx* c) { return c ? c->steps : -1; }
+
+shasta_status shasta_set_step_counter(shasta_ctx* c, int64_t steps) {
+  if (!c) return SHASTA_EINVAL;
+  if (steps < 0) return fail(c, SHASTA_EINVAL, "negative step counter");
+  c->steps = steps;
+  return SHASTA_OK;
+}
+
+shasta_status shasta_counters(shasta_ctx* c, int64_t out[1]) {
+  if (!c || !out) return SHASTA_EINVAL;
+  DeviceGuard dg(c->device);
+  unsigned long long* h = reinterpret_cast<unsigned long long*>(c->h_small + 9);
+  CK(cudaMemcpyAsync(h, c->d_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream),
+     "memcpy counters");
+  CK(cudaStreamSynchronize(c->stream), "sync");
+  out[0] = (int64_t)*h;
+  return SHASTA_OK;
+}
+
+void* shasta_stream(const shasta_ctx* c) { return c ? (void*)c->stream : nullptr; }
+
+const char* shasta_last_error(const shasta_ctx* c) {
+  return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+const char* shasta_status_string(shasta_status s) {
+  switch (s) {
+    case SHASTA_OK: return "SHASTA_OK";
+    case SHASTA_EINVAL: return "SHASTA_EINVAL";
+    case SHASTA_ENOMEM: return "SHASTA_ENOMEM";
+    case SHASTA_EAGAIN: return "SHASTA_EAGAIN";
+    case SHASTA_EUNPHYSICAL: return "SHASTA_EUNPHYSICAL";
+    case SHASTA_ETIMEOUT: return "SHASTA_ETIMEOUT";
+    case SHASTA_ECUDA: return "SHASTA_ECUDA";
+    case SHASTA_ENOTFOUND: return "SHASTA_ENOTFOUND";
+  }
+  return "SHASTA_UNKNOWN";
+}
+
+const char* shasta_version(void) { return kVersion; }
+
+}  // extern "C"

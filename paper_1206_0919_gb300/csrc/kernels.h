@@ -1,0 +1,49 @@
+// kernels.h -- launchers shared between the host API and the kernel units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "sweep.cuh"
+
+namespace shasta {
+
+// Fused sweep launchers, one per precision (sweep_f64.cu, sweep_f32.cu,
+// sweep_mixed.cu).  Return the launch error.
+cudaError_t launch_sweep_f64(const SweepParams& P, int axis, int eos, cudaStream_t s);
+cudaError_t launch_sweep_f32(const SweepParams& P, int axis, int eos, cudaStream_t s);
+cudaError_t launch_sweep_mixed(const SweepParams& P, int axis, int eos, cudaStream_t s);
+
+// Physics constants handed to the auxiliary kernels.
+struct EosParams {
+  int kind;
+  double B, ec;
+  double omd;  // 1 - delta
+};
+
+// Auxiliary kernels (aux.cu).  `is32` selects float (1) or double (0) storage.
+cudaError_t launch_from_f64(const double* src, void* dst, size_t n, int is32, cudaStream_t s);
+cudaError_t launch_to_f64(const void* src, double* dst, size_t n, int is32, cudaStream_t s);
+cudaError_t launch_prim2cons(const double* const prim[5], void* const cons[5], size_t n,
+                             int is32, EosParams eos, cudaStream_t s);
+cudaError_t launch_recover(const void* const cons[5], double* const prim[6], size_t n, int is32,
+                           EosParams eos, cudaStream_t s);
+// Counts cells with non-finite values, E < 0 or |M| >= E (cons) or e < 0,
+// n < 0, |v| >= 1 (prims) into *count (device).
+cudaError_t launch_check_cons(const double* const f[5], size_t n, unsigned long long* count,
+                              cudaStream_t s);
+cudaError_t launch_check_prims(const double* const f[5], size_t n, unsigned long long* count,
+                               cudaStream_t s);
+// Totals: per-block partial sums into `partials` (5 * nblocks doubles, device
+// scratch), then one block sums them in fixed order into out[5] (device).
+int totals_blocks(size_t n);
+cudaError_t launch_totals(const void* const f[5], size_t n, int is32, double* partials,
+                          double* out, cudaStream_t s);
+// Frozen ghost store: for each axis a block [side][layer][field][plane].
+size_t frozen_elems(int nx, int ny, int nz);
+size_t frozen_axis_offset(int nx, int ny, int nz, int axis);
+cudaError_t launch_frozen_capture(const void* const f[5], void* frozen, int nx, int ny, int nz,
+                                  int is32, cudaStream_t s);
+
+}  // namespace shasta

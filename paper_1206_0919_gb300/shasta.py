@@ -1,0 +1,248 @@
+"""Thin ctypes binding of ``libshasta.so`` (the C ABI in include/shasta.h).
+
+Argument marshalling only: every numerical step runs in the library's CUDA
+kernels.  The binding has no fallback: if the library is missing or cannot
+be loaded, importing a solver raises.
+
+Functions with the ABI's names (``shasta_create`` ...) are exported as-is;
+``Solver`` wraps one context for numpy / torch callers.  Arrays are float64,
+shape (nz, ny, nx) (x fastest).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libshasta.so")
+
+OK, EINVAL, ENOMEM, EAGAIN, EUNPHYSICAL, ETIMEOUT, ECUDA, ENOTFOUND = range(8)
+BC_REFLECT, BC_PERIODIC, BC_FROZEN = 0, 1, 2
+EOS_IDEAL, EOS_BAG = 0, 1
+FP64, FP32, MIXED = 0, 1, 2
+MEM_HOST, MEM_DEVICE = 0, 1
+
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "mixed": MIXED}
+BCS = {"reflect": BC_REFLECT, "periodic": BC_PERIODIC, "frozen": BC_FROZEN}
+
+
+class ShastaError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{status_name(status)}: {msg}")
+        self.status = status
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("bc", C.c_int)]
+
+
+class Eos(C.Structure):
+    _fields_ = [("kind", C.c_int), ("B", C.c_double), ("e_c", C.c_double)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("eta", C.c_double), ("delta", C.c_double),
+                ("stream", C.c_void_p), ("device", C.c_int), ("check_input", C.c_int)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+_dp = C.POINTER(C.c_double)
+_vp = C.c_void_p
+
+# name -> (restype, argtypes); the single source of the Python-side ABI.
+SIGNATURES = {
+    "shasta_default_opts": (None, [C.POINTER(Opts)]),
+    "shasta_create": (C.c_int, [C.POINTER(Grid), C.c_double, C.c_double, C.POINTER(Eos),
+                                C.POINTER(Opts), C.POINTER(_vp)]),
+    "shasta_destroy": (C.c_int, [_vp]),
+    "shasta_set_conserved": (C.c_int, [_vp] + [_vp] * 5 + [C.c_int]),
+    "shasta_set_primitives": (C.c_int, [_vp] + [_vp] * 5 + [C.c_int]),
+    "shasta_step": (C.c_int, [_vp, C.c_int]),
+    "shasta_sweep": (C.c_int, [_vp, C.c_int]),
+    "shasta_sync": (C.c_int, [_vp]),
+    "shasta_get_conserved": (C.c_int, [_vp] + [_vp] * 5 + [C.c_int]),
+    "shasta_get_primitives": (C.c_int, [_vp] + [_vp] * 6 + [C.c_int]),
+    "shasta_totals": (C.c_int, [_vp, _dp]),
+    "shasta_steps_done": (C.c_int64, [_vp]),
+    "shasta_set_step_counter": (C.c_int, [_vp, C.c_int64]),
+    "shasta_counters": (C.c_int, [_vp, C.POINTER(C.c_int64)]),
+    "shasta_stream": (_vp, [_vp]),
+    "shasta_last_error": (C.c_char_p, [_vp]),
+    "shasta_status_string": (C.c_char_p, [C.c_int]),
+    "shasta_version": (C.c_char_p, []),
+}
+
+
+def lib():
+    """The loaded library; raises if it is not built (no fallback exists)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(
+                    f"{LIB_PATH} is missing: build it with "
+                    "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
+            L = C.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def status_name(s: int) -> str:
+    try:
+        return lib().shasta_status_string(s).decode()
+    except Exception:  # library not loadable
+        return f"status {s}"
+
+
+def _check(status, ctx=None):
+    if status != OK:
+        msg = lib().shasta_last_error(ctx).decode()
+        raise ShastaError(status, msg)
+
+
+def __getattr__(name):
+    if name in SIGNATURES:
+        return getattr(lib(), name)
+    raise AttributeError(name)
+
+
+# ------------------------------------------------------------- helpers ----
+
+def _host_ptr(a):
+    assert isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _ptrs(arrays):
+    """(pointers, mem, keepalive) for a list of numpy or torch float64 arrays."""
+    if all(a is None for a in arrays):
+        return [None] * len(arrays), MEM_HOST, []
+    first = next(a for a in arrays if a is not None)
+    if _is_torch(first):
+        import torch
+        if first.is_cuda:
+            for a in arrays:
+                if a is not None:
+                    assert a.dtype == torch.float64 and a.is_contiguous() and a.is_cuda
+            return [None if a is None else a.data_ptr() for a in arrays], MEM_DEVICE, arrays
+        keep = [None if a is None else a.contiguous().numpy() for a in arrays]
+        return [None if a is None else _host_ptr(a) for a in keep], MEM_HOST, keep
+    keep = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in arrays]
+    return [None if a is None else _host_ptr(a) for a in keep], MEM_HOST, keep
+
+
+class Solver:
+    """One solver context (one event) of the C ABI."""
+
+    def __init__(self, shape, lam=0.4, dx=1.0, precision="fp32", bc="reflect", eos="ideal",
+                 bag_B=0.1, bag_ec=0.5, eta=0.125, delta=0.0, stream=None, device=0,
+                 check_input=True):
+        L = lib()
+        nx, ny, nz = shape
+        self.shape = (nx, ny, nz)
+        g = Grid(nx, ny, nz, BCS[bc] if isinstance(bc, str) else bc)
+        kind = {"ideal": EOS_IDEAL, "bag": EOS_BAG}[eos] if isinstance(eos, str) else eos
+        e = Eos(kind, bag_B, bag_ec)
+        o = Opts()
+        L.shasta_default_opts(C.byref(o))
+        o.precision = PRECISIONS[precision] if isinstance(precision, str) else precision
+        o.eta = eta
+        o.delta = delta
+        o.stream = stream
+        o.device = device
+        o.check_input = 1 if check_input else 0
+        h = _vp()
+        _check(L.shasta_create(C.byref(g), dx, lam, C.byref(e), C.byref(o), C.byref(h)))
+        self._h = h
+        self.precision = precision
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().shasta_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def grid_shape(self):
+        nx, ny, nz = self.shape
+        return (nz, ny, nx)
+
+    def set_conserved(self, U):
+        p, mem, keep = _ptrs(list(U))
+        _check(lib().shasta_set_conserved(self._h, *p, mem), self._h)
+
+    def set_primitives(self, e, vx, vy, vz, n):
+        p, mem, keep = _ptrs([e, vx, vy, vz, n])
+        _check(lib().shasta_set_primitives(self._h, *p, mem), self._h)
+
+    def step(self, nsteps=1):
+        _check(lib().shasta_step(self._h, int(nsteps)), self._h)
+
+    def sweep(self, axis):
+        _check(lib().shasta_sweep(self._h, int(axis)), self._h)
+
+    def sync(self):
+        _check(lib().shasta_sync(self._h), self._h)
+
+    def get_conserved(self, out=None):
+        if out is None:
+            out = [np.empty(self.grid_shape) for _ in range(5)]
+        p, mem, keep = _ptrs(list(out))
+        _check(lib().shasta_get_conserved(self._h, *p, mem), self._h)
+        return out
+
+    def get_primitives(self, out=None):
+        if out is None:
+            out = [np.empty(self.grid_shape) for _ in range(6)]
+        p, mem, keep = _ptrs(list(out))
+        _check(lib().shasta_get_primitives(self._h, *p, mem), self._h)
+        return dict(zip(("e", "vx", "vy", "vz", "n", "p"), out))
+
+    def totals(self):
+        out = (C.c_double * 5)()
+        _check(lib().shasta_totals(self._h, out), self._h)
+        return np.array(out[:])
+
+    @property
+    def steps_done(self):
+        return int(lib().shasta_steps_done(self._h))
+
+    def set_step_counter(self, n):
+        _check(lib().shasta_set_step_counter(self._h, int(n)), self._h)
+
+    def counters(self):
+        out = (C.c_int64 * 1)()
+        _check(lib().shasta_counters(self._h, out), self._h)
+        return int(out[0])
+
+    @property
+    def stream(self):
+        return lib().shasta_stream(self._h)

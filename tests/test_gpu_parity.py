@@ -1,0 +1,194 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+FP64: at most 1e-12 relative error per cell (the kernels evaluate the same
+expressions in the same order without FMA contraction, so most cells agree
+bitwise).  FP32 and mixed: at most 1e-4 relative L1 error in e and 1e-5
+relative drift of the conserved totals against the oracle.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import max_rel_err, oracle, rel_l1
+from oracle import oracle as OR
+from paper_1206_0919_gb300 import shasta as S
+from paper_1206_0919_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+BC_NAMES = {OR.BC_REFLECT: "reflect", OR.BC_PERIODIC: "periodic", OR.BC_FROZEN: "frozen"}
+EOS_NAMES = {OR.EOS_IDEAL: "ideal", OR.EOS_BAG: "bag"}
+
+
+def run_gpu(shape, U0, nsteps, precision, bc=OR.BC_REFLECT, eos=OR.EOS_IDEAL, lam=0.4,
+            eta=0.125, step0=0):
+    with S.Solver(shape, lam=lam, precision=precision, bc=BC_NAMES[bc], eos=EOS_NAMES[eos],
+                  eta=eta) as s:
+        s.set_conserved(U0)
+        if step0:
+            s.set_step_counter(step0)
+        s.step(nsteps)
+        return s.get_conserved(), s.get_primitives(), s.totals()
+
+
+def fp64_check(shape, U0, nsteps, bc=OR.BC_REFLECT, eos=OR.EOS_IDEAL, tol=1e-12, step0=0,
+               lam=0.4):
+    O = oracle()
+    P = OR.params(shape, bc=bc, eos=eos, lam=lam)
+    ref = O.step(P, U0, nsteps, step0=step0)
+    got, prim, tot = run_gpu(shape, U0, nsteps, "fp64", bc=bc, eos=eos, step0=step0, lam=lam)
+    errs = [max_rel_err(g, o) for g, o in zip(got, ref)]
+    assert max(errs) <= tol, f"FP64 per-cell relative error {errs}"
+    rp = O.recover(P, ref)
+    for k in ("e", "vx", "vy", "vz", "n", "p"):
+        e = max_rel_err(prim[k], rp[k])
+        assert e <= 10 * tol, f"primitive {k}: {e}"
+    rt = O.totals(ref)
+    scale = np.array([np.abs(u).sum() for u in ref])
+    assert np.all(np.abs(tot - rt) <= 1e-13 * scale + 1e-300), (tot, rt)
+    return errs
+
+
+def test_fp64_config1_shock_tube():
+    """64^3 planar Riemann shock tube, FP64, 40 full split steps."""
+    shape = (64, 64, 64)
+    P = OR.params(shape)
+    U0 = oracle().prim2cons(P, *W.shock_tube(*shape).as_list())
+    fp64_check(shape, U0, 40)
+
+
+@pytest.mark.parametrize("bc", [OR.BC_REFLECT, OR.BC_PERIODIC, OR.BC_FROZEN])
+@pytest.mark.parametrize("eos", [OR.EOS_IDEAL, OR.EOS_BAG])
+@pytest.mark.parametrize("shape", [(13, 9, 7), (37, 21, 5), (3, 5, 2), (1, 1, 1), (40, 1, 1),
+                                   (1, 33, 1), (2, 1, 29)])
+def test_fp64_random_states(shape, bc, eos):
+    """Ragged shapes, short lines (n < ghost depth), all boundary rules and
+    both EoS on a random state with |v| up to 0.6; 7 steps cover every entry
+    of the axis table."""
+    pr = W.random_state(shape, seed=sum(shape) + 10 * bc + 100 * eos, vmax=0.6,
+                        e_range=(0.3, 3.0) if eos == OR.EOS_BAG else (0.05, 5.0))
+    P = OR.params(shape, bc=bc, eos=eos)
+    U0 = oracle().prim2cons(P, *pr.as_list())
+    fp64_check(shape, U0, 7, bc=bc, eos=eos)
+
+
+def test_fp64_step_phase_and_resume():
+    """Starting at another step counter follows the table from that phase;
+    checkpoint/resume through get/set_conserved is bitwise."""
+    shape = (20, 18, 16)
+    pr = W.hot_spots(shape=shape, seed=5, n_spots=5, sigma=(1.5, 3), radial_flow=0.1)
+    P = OR.params(shape)
+    U0 = oracle().prim2cons(P, *pr.as_list())
+    fp64_check(shape, U0, 4, step0=3)
+    with S.Solver(shape, precision="fp64") as a, S.Solver(shape, precision="fp64") as b:
+        a.set_conserved(U0)
+        a.step(10)
+        full = a.get_conserved()
+        b.set_conserved(U0)
+        b.step(4)
+        mid = b.get_conserved()
+        n = b.steps_done
+        b.set_conserved(mid)
+        b.set_step_counter(n)
+        b.step(6)
+        res = b.get_conserved()
+    for x, y in zip(full, res):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_fp32_config1_shock_tube(precision):
+    shape = (64, 64, 64)
+    O = oracle()
+    P = OR.params(shape)
+    U0 = O.prim2cons(P, *W.shock_tube(*shape).as_list())
+    ref = O.step(P, U0, 40)
+    got, prim, tot = run_gpu(shape, U0, 40, precision)
+    e_ref = O.recover(P, ref)["e"]
+    assert rel_l1(prim["e"], e_ref) <= 1e-4
+    t0, t1 = O.totals(U0), O.totals(ref)
+    for k in (0, 4):
+        assert abs(tot[k] - t1[k]) <= 1e-5 * abs(t0[k])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_fp32_hot_spots(precision):
+    """Config-2 recipe (Gaussian hot spots on 1e-6, n = e^(3/4)) at 64^3, 40 steps."""
+    shape = (64, 64, 64)
+    O = oracle()
+    P = OR.params(shape)
+    U0 = O.prim2cons(P, *W.hot_spots(N=64, seed=2, n_spots=30).as_list())
+    ref = O.step(P, U0, 40)
+    got, prim, tot = run_gpu(shape, U0, 40, precision)
+    e_ref = O.recover(P, ref)["e"]
+    err = rel_l1(prim["e"], e_ref)
+    assert err <= 1e-4, err
+    t0 = O.totals(U0)
+    t1 = O.totals(ref)
+    for k in (0, 4):
+        assert abs(tot[k] - t1[k]) <= 1e-5 * abs(t0[k]), (k, tot[k], t1[k])
+
+
+def test_set_primitives_matches_oracle_map():
+    shape = (17, 11, 6)
+    pr = W.random_state(shape, seed=3, vmax=0.9)
+    O = oracle()
+    for eos in (OR.EOS_IDEAL, OR.EOS_BAG):
+        P = OR.params(shape, eos=eos)
+        ref = O.prim2cons(P, *pr.as_list())
+        with S.Solver(shape, precision="fp64", eos=EOS_NAMES[eos]) as s:
+            s.set_primitives(*pr.as_list())
+            got = s.get_conserved()
+        for g, o in zip(got, ref):
+            assert np.array_equal(g, o)
+
+
+def test_device_memory_paths():
+    """DEVICE-memory set/get through torch CUDA tensors equals the host path."""
+    import torch
+    shape = (16, 12, 8)
+    pr = W.random_state(shape, seed=4)
+    O = oracle()
+    U0 = O.prim2cons(OR.params(shape), *pr.as_list())
+    with S.Solver(shape, precision="fp64") as s:
+        s.set_conserved([torch.from_numpy(u).cuda() for u in U0])
+        s.step(2)
+        out = [torch.empty(u.shape, dtype=torch.float64, device="cuda") for u in U0]
+        s.get_conserved(out)
+        host = s.get_conserved()
+    for d, h in zip(out, host):
+        assert np.array_equal(d.cpu().numpy(), h)
+
+
+def test_errors():
+    with pytest.raises(S.ShastaError) as ei:
+        S.Solver((0, 4, 4))
+    assert ei.value.status == S.EINVAL
+    with pytest.raises(S.ShastaError):
+        S.Solver((4, 4, 4), lam=0.7)
+    with S.Solver((4, 4, 4)) as s:
+        with pytest.raises(S.ShastaError) as ei:
+            s.step(1)
+        assert ei.value.status == S.EINVAL
+        bad = [np.ones((4, 4, 4)) for _ in range(5)]
+        bad[1][0, 0, 0] = 2.0  # |M| > E
+        with pytest.raises(S.ShastaError) as ei:
+            s.set_conserved(bad)
+        assert ei.value.status == S.EUNPHYSICAL
+        bad[1][0, 0, 0] = np.nan
+        with pytest.raises(S.ShastaError) as ei:
+            s.set_conserved(bad)
+        assert ei.value.status == S.EUNPHYSICAL
+
+
+def test_full_size_one_step_fp32():
+    """200^3 hot spots (the benchmark workload), one step of the benchmark's
+    FP32 kernel, every cell against the oracle."""
+    O = oracle()
+    shape = (200, 200, 200)
+    P = OR.params(shape)
+    U0 = O.prim2cons(P, *W.hot_spots(N=200, seed=2).as_list())
+    ref = O.step(P, U0, 1)
+    got, prim, tot = run_gpu(shape, U0, 1, "fp32")
+    for k, (g, o) in enumerate(zip(got, ref)):
+        assert rel_l1(g, o) <= 1e-6, (k, rel_l1(g, o))
+    assert rel_l1(prim["e"], O.recover(P, ref)["e"]) <= 1e-6
