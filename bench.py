@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--e2e-events", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true")
+    ap.add_argument("--mode", choices=["full", "kernels"], default="full",
+                    help="kernels: only warmup + K steps (for profiler captures)")
     return ap.parse_args()
 
 
@@ -389,10 +391,33 @@ def run_ours(args):
     return 0
 
 
+def run_kernels_only(args):
+    """Set the state, W warmup steps, K steps; nothing else (profiling)."""
+    import torch
+
+    from paper_1206_0919_gb300 import shasta as S
+
+    N = args.grid
+    s = S.Solver((N, N, N), precision=args.precision)
+    s.set_primitives(*workload_prims(N).as_list())
+    s.step(args.warmup)
+    s.sync()
+    t = time.perf_counter()
+    s.step(args.steps)
+    s.sync()
+    dt = time.perf_counter() - t
+    print(json.dumps({"mode": "kernels", "precision": args.precision, "grid": N,
+                      "steps": args.steps, "wall_ms_per_step": dt * 1e3 / max(1, args.steps)}))
+    s.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "kernels":
+        return run_kernels_only(args)
     return run_ours(args)
 
 

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <new>
@@ -45,6 +46,10 @@ struct shasta_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int64_t steps = 0;
+  int sm_count = 152;
+  int warps_per_sm = 12;  // segment target of the FP32 kernels
+  int force_nseg = 0;     // nonzero: segments per line (tuning)
+  int variant = 0;        // launch variant of the FP32 kernels (tuning)
   std::string err;
 };
 
@@ -190,6 +195,24 @@ SweepParams sweep_params(shasta_ctx* c, int axis, int from) {
   P.bag_B = c->eos.B;
   P.bag_ec = c->eos.e_c;
   P.clamp_count = c->d_count;
+  // Lines are cut into segments until the launch has about warps_per_sm
+  // warps per SM (each segment re-reads a 6-cell halo per side).
+  int nseg = 1;
+  if (c->o.precision != SHASTA_FP64) {
+    const long long groups = (P.plane + 31) / 32;
+    const long long target = (long long)c->sm_count * c->warps_per_sm;
+    nseg = (int)((target + groups - 1) / groups);
+    const int max_seg = P.n / 32 > 1 ? P.n / 32 : 1;
+    if (nseg > max_seg) nseg = max_seg;
+    if (c->force_nseg > 0) nseg = c->force_nseg;
+    if (nseg < 1) nseg = 1;
+  }
+  int seg = (P.n + nseg - 1) / nseg;
+  seg = (seg + 7) & ~7;
+  P.seg_len = seg;
+  P.nseg = (P.n + seg - 1) / seg;
+  P.fstride = (long long)((char*)c->buf[0][1] - (char*)c->buf[0][0]) / (long long)c->esize;
+  P.variant = c->variant;
   return P;
 }
 
@@ -290,6 +313,17 @@ shasta_status shasta_create(const shasta_grid* g, double dx, double lambda, cons
   c->is32 = opts.precision != SHASTA_FP64;
   c->esize = c->is32 ? 4 : 8;
   c->ncell = (size_t)g->nx * g->ny * g->nz;
+  {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) == cudaSuccess && sms > 0)
+      c->sm_count = sms;
+    const char* v = getenv("SHASTA_WARPS_PER_SM");
+    if (v && atoi(v) > 0) c->warps_per_sm = atoi(v);
+    v = getenv("SHASTA_NSEG");
+    if (v && atoi(v) > 0) c->force_nseg = atoi(v);
+    v = getenv("SHASTA_VARIANT");
+    if (v) c->variant = atoi(v);
+  }
   auto bail = [&](cudaError_t err, const char* where) {
     std::string m = std::string(where) + ": " + cudaGetErrorString(err);
     release(c);

@@ -59,6 +59,10 @@ struct SweepParams {
   double omd;             // 1 - delta (clamp of |M|)
   double bag_B, bag_ec;
   unsigned long long* clamp_count;  // cells recovered with |M| clamped or E <= 0
+  int seg_len;                      // fast kernels: cells per line segment (multiple of 8)
+  int nseg;                         // fast kernels: segments per line
+  long long fstride;                // fast kernels: in[k] = in[0] + k*fstride (same for out)
+  int variant;                      // fast kernels: launch variant (0: 3 CTAs/SM, 1: 2 CTAs/SM)
 };
 
 // ------------------------------------------------------------- recovery ----
@@ -101,14 +105,14 @@ __device__ __forceinline__ void eos_solve(R E, R M, R B, R ec, R& e, R& p) {
 // Velocity along the sweep axis and pressure of one cell.  m1 is the
 // momentum along the sweep, m2/m3 the other two in increasing axis order;
 // |M|^2 is summed in x, y, z order.
+// Returns 1 if |M| was clamped or E <= 0, else 0.
 template <class R, int EOS, int AXIS>
-__device__ __forceinline__ void recover_wp(R E, R m1, R m2, R m3, R omd, R B, R ec, R& w, R& p,
-                                           unsigned& nclamp) {
+__device__ __forceinline__ unsigned recover_wp(R E, R m1, R m2, R m3, R omd, R B, R ec, R& w,
+                                               R& p) {
   if (!(E > R(0))) {
     w = R(0);
     p = R(0);
-    ++nclamp;
-    return;
+    return 1;
   }
   R X = AXIS == 0 ? m1 : m2;
   R Y = AXIS == 0 ? m2 : (AXIS == 1 ? m1 : m3);
@@ -116,16 +120,18 @@ __device__ __forceinline__ void recover_wp(R E, R m1, R m2, R m3, R omd, R B, R 
   R M = sqrt((X * X + Y * Y) + Z * Z);
   R lim = omd * E;
   R m = m1;
+  unsigned clamped = 0;
   if (M > lim) {
     m = m1 * (lim / M);
     M = lim;
-    ++nclamp;
+    clamped = 1;
   }
   R e, pp;
   eos_solve<R, EOS>(E, M, B, ec, e, pp);
   R h = E + pp;
   w = m / h;
   p = pp;
+  return clamped;
 }
 
 // ------------------------------------------------------------ transport ----
@@ -298,8 +304,9 @@ __global__ void __launch_bounds__(128) sweep_kernel(SweepParams P) {
     pn[1] = pn[2];
     {
       R w, p;
-      recover_wp<R, EOS, AXIS>(R(u[7][0]), R(u[7][1]), R(u[7][2]), R(u[7][3]), omd, B, ec, w, p,
-                               nclamp);
+      const unsigned c0 = recover_wp<R, EOS, AXIS>(R(u[7][0]), R(u[7][1]), R(u[7][2]),
+                                                   R(u[7][3]), omd, B, ec, w, p);
+      nclamp += (q >= 0 && q < n) ? c0 : 0u;
       wn[2] = T(w);
       pn[2] = T(p);
     }
@@ -338,7 +345,9 @@ __global__ void __launch_bounds__(128) sweep_kernel(SweepParams P) {
     ph[1] = ph[2];
     {
       R w, p;
-      recover_wp<R, EOS, AXIS>(R(hs[0]), R(hs[1]), R(hs[2]), R(hs[3]), omd, B, ec, w, p, nclamp);
+      const unsigned c3 =
+          recover_wp<R, EOS, AXIS>(R(hs[0]), R(hs[1]), R(hs[2]), R(hs[3]), omd, B, ec, w, p);
+      nclamp += (jh >= 0 && jh < n) ? c3 : 0u;
       wh[2] = T(w);
       ph[2] = T(p);
     }

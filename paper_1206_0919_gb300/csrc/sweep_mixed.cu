@@ -1,15 +1,32 @@
-// sweep_mixed.cu -- MIXED: state, transport and limiter in float, recovery in double.
+// sweep_mixed.cu -- MIXED: state, transport and limiter in float; the recovery's E^2 - |M|^2 in double-float.
 #include "kernels.h"
+#include "sweep_fast.cuh"
 
 namespace shasta {
 
-template <int EOS, int AXIS>
-static cudaError_t go(const SweepParams& P, cudaStream_t s) {
-  const int threads = 128;
-  long long blocks = (P.plane + threads - 1) / threads;
-  sweep_kernel<float, double, EOS, AXIS, true><<<(unsigned)blocks, threads, 0, s>>>(P);
+namespace {
+
+constexpr int kWarps = 4, kRing = 8, kDist = 4;
+
+template <int EOS, int AXIS, int MINB>
+cudaError_t go2(const SweepParams& P, cudaStream_t s) {
+  auto k = fast::sweep_fast_kernel<EOS, AXIS, true, kWarps, kRing, kDist, MINB>;
+  const size_t smem = (size_t)kWarps * fast::Smem<AXIS, kRing>::per_warp * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long warps = ((P.plane + 31) / 32) * P.nseg;
+  const long long blocks = (warps + kWarps - 1) / kWarps;
+  k<<<(unsigned)blocks, kWarps * 32, smem, s>>>(P);
   return cudaGetLastError();
 }
+
+// variant 0: registers capped for 3 CTAs (12 warps) per SM; 1: uncapped.
+template <int EOS, int AXIS>
+cudaError_t go(const SweepParams& P, cudaStream_t s) {
+  return P.variant == 1 ? go2<EOS, AXIS, 1>(P, s) : go2<EOS, AXIS, 3>(P, s);
+}
+
+}  // namespace
 
 cudaError_t launch_sweep_mixed(const SweepParams& P, int axis, int eos, cudaStream_t s) {
   if (P.plane <= 0) return cudaSuccess;

@@ -192,3 +192,46 @@ def test_full_size_one_step_fp32():
     for k, (g, o) in enumerate(zip(got, ref)):
         assert rel_l1(g, o) <= 1e-6, (k, rel_l1(g, o))
     assert rel_l1(prim["e"], O.recover(P, ref)["e"]) <= 1e-6
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+@pytest.mark.parametrize("bc", [OR.BC_REFLECT, OR.BC_PERIODIC, OR.BC_FROZEN])
+@pytest.mark.parametrize("eos", [OR.EOS_IDEAL, OR.EOS_BAG])
+@pytest.mark.parametrize("shape,nseg", [((37, 21, 13), 0), ((64, 40, 9), 3), ((3, 5, 2), 0),
+                                        ((40, 1, 1), 0), ((1, 33, 1), 0), ((2, 1, 29), 0),
+                                        ((70, 66, 65), 2), ((97, 35, 8), 5)])
+def test_fp32_random_states(monkeypatch, shape, nseg, bc, eos, precision):
+    """The FP32 kernels on ragged shapes, forced line segmentation (several
+    segments per line, halo re-read), short lines, every boundary rule and
+    both EoS: relative L1 error per field against the FP64 oracle."""
+    if nseg:
+        monkeypatch.setenv("SHASTA_NSEG", str(nseg))
+    pr = W.random_state(shape, seed=sum(shape) + 10 * bc + 100 * eos, vmax=0.6,
+                        e_range=(0.3, 3.0) if eos == OR.EOS_BAG else (0.05, 5.0))
+    O = oracle()
+    P = OR.params(shape, bc=bc, eos=eos)
+    U0 = O.prim2cons(P, *pr.as_list())
+    ref = O.step(P, U0, 3)
+    got, prim, tot = run_gpu(shape, U0, 3, precision, bc=bc, eos=eos)
+    errs = [rel_l1(g, o) for g, o in zip(got, ref)]
+    assert max(errs) <= 2e-5, errs
+    assert rel_l1(prim["e"], O.recover(P, ref)["e"]) <= 2e-5
+
+
+def test_clamp_counter():
+    """No clamps on a smooth subluminal flow; an injected |M| > E cell is counted."""
+    shape = (16, 8, 8)
+    pr = W.hot_spots(shape=shape, seed=9, n_spots=3, sigma=(2.0, 3.0), background=0.1,
+                     radial_flow=0.2)
+    U0 = oracle().prim2cons(OR.params(shape), *pr.as_list())
+    for precision in ("fp64", "fp32"):
+        with S.Solver(shape, precision=precision) as s:
+            s.set_conserved(U0)
+            s.step(2)
+            assert s.counters() == 0
+        bad = [u.copy() for u in U0]
+        bad[1][3, 3, 3] = 1.5 * bad[0][3, 3, 3]  # |M| > E in one cell
+        with S.Solver(shape, precision=precision, check_input=False) as s:
+            s.set_conserved(bad)
+            s.sweep(0)
+            assert s.counters() >= 1
