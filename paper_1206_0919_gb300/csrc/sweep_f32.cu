@@ -6,7 +6,7 @@ namespace shasta {
 
 namespace {
 
-constexpr int kWarps = 4, kRing = 8, kDist = 4;
+constexpr int kWarps = 4, kRing = 8, kDist = 3;
 
 template <int EOS, int AXIS, int MINB>
 cudaError_t go2(const SweepParams& P, cudaStream_t s) {

@@ -2,7 +2,7 @@
 //
 // Same sweep as sweep.cuh (arXiv:1206.0919, Sec. 3: half step with lambda/2,
 // recovery at n+1/2, full step from the old state), reorganised for
-// throughput:
+// throughput on Blackwell:
 //
 //  * One warp streams 32 lines (one per lane) along the sweep axis.  Lines
 //    may be cut into segments (each with its own 6-cell halo per side) so
@@ -14,8 +14,14 @@
 //    per 32-byte row segment) and writes results back the same way from the
 //    ring entries it no longer needs, so global accesses stay
 //    sector-complete.
+//  * The five fields travel as two packed pairs, (E, M_par) and
+//    (M_t1, M_t2), plus R: transport, differences and the antidiffusive
+//    flux use the packed f32x2 add/sub/mul/fma of sm_100+ (two fields per
+//    instruction); the flux limiter uses the three-input min.
 //  * The loop is unrolled by 4 and every register window is a circular
-//    buffer indexed at compile time: no window shifting.
+//    buffer indexed at compile time: no window shifting.  Blocks of
+//    iterations that touch no ghost position run a variant without boundary
+//    logic.
 //  * The old state for the full step is re-read from the ring (it is still
 //    resident) instead of being carried in registers.
 //  * Transport factors use Q-_j = 1 - Q+_{j-1}, exact for Eq. shasta-diff
@@ -37,9 +43,56 @@ namespace shasta {
 namespace fast {
 
 constexpr int LANES = 32;
-constexpr int CH = 8;         // x sweep: positions per cooperative chunk
-constexpr int XSTR = CH + 1;  // padded row of a chunk tile (conflict-free reads)
-constexpr int XSLOTS = 3;     // x sweep: chunk slots (previous, current, next)
+constexpr int CH = 8;      // x sweep: positions per cooperative chunk
+constexpr int XSLOTS = 3;  // x sweep: chunk slots (previous, current, next)
+// x ring slot: pair planes [row][pos][2] with row stride 18 (conflict-free
+// 64-bit reads down a column), R plane [row][pos] with row stride 9.
+constexpr int XPSTR = 2 * CH + 2;
+constexpr int XRSTR = CH + 1;
+constexpr int XPAIR = LANES * XPSTR;              // 576 floats
+constexpr int XSLOT = 2 * XPAIR + LANES * XRSTR;  // 1440 floats
+// y/z ring slot: pair rows [lane][2] (64 floats each), R row [lane]
+constexpr int YSLOT = 2 * 2 * LANES + LANES;      // 160 floats
+
+// ------------------------------------------------------- packed f32x2 ----
+
+typedef unsigned long long f2;  // two floats in one 64-bit register pair (lo, hi)
+
+__device__ __forceinline__ f2 pk(float lo, float hi) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void up(f2 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+  f2 r;
+  asm("add.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+  f2 r;
+  asm("sub.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+  f2 r;
+  asm("mul.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+  f2 r;
+  asm("fma.rn.ftz.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+// negates the high half (M_par of pair (E, M_par))
+__device__ __forceinline__ f2 neg_hi(f2 v) { return v ^ 0x8000000000000000ull; }
 
 // ---------------------------------------------------------- cp.async ----
 
@@ -76,7 +129,7 @@ __device__ __forceinline__ bool flips(int q, int n, int bc) {
   return m >= n;
 }
 
-// Global field index of sweep-order field f.
+// Global field index of sweep-order field f (E, M_par, M_t1, M_t2, R).
 template <int AXIS>
 __device__ __forceinline__ int gfield(int f) {
   constexpr int FPAR = 1 + AXIS;
@@ -97,6 +150,17 @@ __device__ __forceinline__ const float* src_addr(const SweepParams& P, int f, lo
     return static_cast<const float*>(P.frozen) + ((long long)(side * NG + layer) * NF + gf) * P.plane + t;
   }
   return static_cast<const float*>(P.in[gf]) + base + (long long)map_pos(q, n, P.bc) * P.stride;
+}
+
+// Offset of sweep-order field f of a position inside a ring slot.
+template <bool XP>
+__device__ __forceinline__ int ring_off(int f, int row, int pos) {
+  if (XP) {
+    if (f < 4) return (f >> 1) * XPAIR + row * XPSTR + pos * 2 + (f & 1);
+    return 2 * XPAIR + row * XRSTR + pos;
+  }
+  if (f < 4) return (f >> 1) * (2 * LANES) + row * 2 + (f & 1);
+  return 4 * LANES + row;
 }
 
 // ----------------------------------------------------------- recovery ----
@@ -164,40 +228,216 @@ __device__ __forceinline__ unsigned rec32(float E, float m1, float m2, float m3,
   return clamped;
 }
 
-// Limited phoenical antidiffusive flux through face j+1/2 (Sec. 3) from the
-// transported values at j-1..j+2 and the old differences Delta_{j-1},
-// Delta_j, Delta_{j+1}; the sign of A^ph is applied with sign-bit flips.
-__device__ __forceinline__ float afx(float h0, float h1, float h2, float h3, float dm, float d,
-                                     float dp, float eta) {
-  const float dhm = h1 - h0;
-  const float dh = h2 - h1;
-  const float dhp = h3 - h2;
-  const float aph = eta * fmaf(-0.125f, (dp + dm) - 2.0f * d, dh);
+// Two independent recoveries at once (halves lo, hi), ideal gas, packed.
+// Clamped or vacuum cells fall back to the scalar routine.  Returns the
+// clamp flag of the lo half.
+template <int EOS, bool MIXED>
+__device__ __forceinline__ unsigned rec2(f2 E, f2 m1, f2 m2, f2 m3, f2 omd2, float omd, float B,
+                                         float ec, f2& w, f2& p) {
+  if (EOS == EOS_BAG || MIXED) {
+    float El, Eh, al, ah, bl, bh, cl, ch, wl, wh_, pl, ph;
+    up(E, El, Eh);
+    up(m1, al, ah);
+    up(m2, bl, bh);
+    up(m3, cl, ch);
+    const unsigned c = rec32<EOS, MIXED>(El, al, bl, cl, omd, B, ec, wl, pl);
+    rec32<EOS, MIXED>(Eh, ah, bh, ch, omd, B, ec, wh_, ph);
+    w = pk(wl, wh_);
+    p = pk(pl, ph);
+    return c;
+  }
+  const f2 M2 = fma2(m1, m1, fma2(m2, m2, mul2(m3, m3)));
+  const f2 E2 = mul2(E, E);
+  const f2 lim = mul2(omd2, E);
+  const f2 L2 = mul2(lim, lim);
+  float M2l, M2h, L2l, L2h, El, Eh;
+  up(M2, M2l, M2h);
+  up(L2, L2l, L2h);
+  up(E, El, Eh);
+  if (M2l > L2l || M2h > L2h || !(El > 0.0f) || !(Eh > 0.0f)) {
+    float al, ah, bl, bh, cl, ch, wl, wh_, pl, ph;
+    up(m1, al, ah);
+    up(m2, bl, bh);
+    up(m3, cl, ch);
+    const unsigned c = rec32<EOS, MIXED>(El, al, bl, cl, omd, B, ec, wl, pl);
+    rec32<EOS, MIXED>(Eh, ah, bh, ch, omd, B, ec, wh_, ph);
+    w = pk(wl, wh_);
+    p = pk(pl, ph);
+    return c;
+  }
+  const f2 D = sub2(E2, M2);
+  float tl, th;
+  up(fma2(pk(3.0f, 3.0f), D, E2), tl, th);
+  const f2 den = add2(E, pk(sqrtf(tl), sqrtf(th)));
+  float dl, dh;
+  up(den, dl, dh);
+  p = mul2(D, pk(__fdividef(1.0f, dl), __fdividef(1.0f, dh)));
+  float hl, hh;
+  up(add2(E, p), hl, hh);
+  w = mul2(m1, pk(__fdividef(1.0f, hl), __fdividef(1.0f, hh)));
+  return 0u;
+}
+
+// ------------------------------------------------------- antidiffusion ----
+
+// Flux limiter of Sec. 3 on one field: A = s max(0, min(s dhp, |aph|, s dhm))
+// with s = sgn(aph), applied through sign-bit flips (aph = 0 gives 0).
+__device__ __forceinline__ float limit(float aph, float dhp, float dhm) {
   const uint32_t sg = __float_as_uint(aph) & 0x80000000u;
   const float p1 = __uint_as_float(__float_as_uint(dhp) ^ sg);
   const float p2 = __uint_as_float(__float_as_uint(dhm) ^ sg);
-  const float mm = fmaxf(0.0f, fminf(fminf(p1, fabsf(aph)), p2));
+  const float mm = fmaxf(0.0f, min3f(p1, fabsf(aph), p2));
   return __uint_as_float(__float_as_uint(mm) ^ sg);
+}
+
+// Limited phoenical antidiffusive flux through face j+1/2 for a field pair,
+// from the transported values at j-1..j+2 and the old differences
+// Delta_{j-1}, Delta_j, Delta_{j+1}.  The sign s = sgn(aph) (+1 for +0) is
+// applied by packed multiplies: A = s max(0, min(s dhp, s aph, s dhm)).
+__device__ __forceinline__ f2 afx2(f2 h0, f2 h1, f2 h2, f2 h3, f2 dm, f2 d, f2 dp, f2 eta2,
+                                   f2 m2, f2 m8) {
+  const f2 dhm = sub2(h1, h0);
+  const f2 dh = sub2(h2, h1);
+  const f2 dhp = sub2(h3, h2);
+  const f2 aph = mul2(eta2, fma2(m8, fma2(m2, d, add2(dp, dm)), dh));
+  const f2 sg = (aph & 0x8000000080000000ull) | 0x3f8000003f800000ull;  // +-1 per half
+  float p0, p1, a0, a1, q0, q1;
+  up(mul2(sg, dhp), p0, p1);
+  up(mul2(sg, aph), a0, a1);
+  up(mul2(sg, dhm), q0, q1);
+  return mul2(sg, pk(fmaxf(min3f(p0, a0, q0), 0.0f), fmaxf(min3f(p1, a1, q1), 0.0f)));
+}
+
+__device__ __forceinline__ float afx1(float h0, float h1, float h2, float h3, float dm, float d,
+                                      float dp, float eta) {
+  const float dhm = h1 - h0;
+  const float dh = h2 - h1;
+  const float dhp = h3 - h2;
+  const float aph = eta * fmaf(-0.125f, fmaf(-2.0f, d, dp + dm), dh);
+  return limit(aph, dhp, dhm);
 }
 
 // Shared memory per warp, in floats.
 template <int AXIS, int RING>
 struct Smem {
-  static constexpr int per_warp =
-      AXIS == 0 ? XSLOTS * NF * LANES * XSTR : RING * NF * LANES;
+  static constexpr int per_warp = AXIS == 0 ? XSLOTS * XSLOT : RING * YSLOT;
 };
-
-// ------------------------------------------------------------- kernel ----
 
 template <int V>
 using ic = std::integral_constant<int, V>;
 template <bool V>
 using bc_ = std::integral_constant<bool, V>;
 
+// ------------------------------------------------------ line pipeline ----
+//
+// One SHASTA pass of a field pair along the line, written with differences
+// so that every carried quantity is needed for at most two positions.  With
+// the newest cell k (U_k just read), one step computes
+//   Delta_{k-1} = U_k - U_{k-1}
+//   Uhat_{k-1}  = a Delta_{k-1} + nb Delta_{k-2} + c U_{k-1} (+ source)      [Eq. shasta-geo]
+//   DD_{k-1}    = Delta_{k-1} - Delta_{k-2},  D2_{k-2} = DD_{k-1} - DD_{k-2}
+//   Dh_{k-2}    = Uhat_{k-1} - Uhat_{k-2}                                   [Delta-hat]
+//   A_{k-3}     = limit(eta (Dh_{k-3} - D2_{k-3}/8), Dh_{k-2}, Dh_{k-4})    [phoenical + limiter]
+//   out_{k-3}   = Uhat_{k-3} - (A_{k-3} - A_{k-4})                          [Eq. shasta-n]
+// Two-slot arrays are indexed by position parity; K is the parity of k.
+struct Line2 {
+  f2 Up;     // U_{k-1}
+  f2 D[2];   // Delta by parity
+  f2 DD[2];  // first difference of Delta
+  f2 D2[2];  // second difference of Delta
+  f2 Uh[2];  // transported values
+  f2 Dh[2];  // their differences
+  f2 A;      // limited flux of the previous face
+};
+struct Line1 {
+  float Up, D[2], DD[2], D2[2], Uh[2], Dh[2], A;
+};
+
+template <int K, bool SRC>
+__device__ __forceinline__ f2 step2(Line2& s, f2 u, f2 a2, f2 nb2, f2 c2, f2 src, f2 eta2, f2 m8) {
+  constexpr int P0 = K & 1, P1 = (K + 1) & 1;  // parity of k (= k-2, k-4) and of k-1 (= k-3)
+  const f2 d = sub2(u, s.Up);                                    // Delta_{k-1}
+  f2 uh = fma2(c2, s.Up, fma2(a2, d, mul2(nb2, s.D[P0])));       // Uhat_{k-1}
+  if (SRC) uh = add2(uh, src);
+  const f2 dd = sub2(d, s.D[P0]);                                // DD_{k-1}
+  const f2 d2 = sub2(dd, s.DD[P0]);                              // D2_{k-2}
+  const f2 dh = sub2(uh, s.Uh[P0]);                              // Dh_{k-2}
+  const f2 aph = mul2(eta2, fma2(m8, s.D2[P1], s.Dh[P1]));        // A^ph_{k-3}
+  const f2 sg = (aph & 0x8000000080000000ull) | 0x3f8000003f800000ull;
+  float p0, p1, a0, a1, q0, q1;
+  up(mul2(sg, dh), p0, p1);
+  up(mul2(sg, aph), a0, a1);
+  up(mul2(sg, s.Dh[P0]), q0, q1);
+  const f2 A = mul2(sg, pk(fmaxf(min3f(p0, a0, q0), 0.0f), fmaxf(min3f(p1, a1, q1), 0.0f)));
+  const f2 out = sub2(s.Uh[P1], sub2(A, s.A));                   // out_{k-3}
+  s.A = A;
+  s.Up = u;
+  s.D[P1] = d;
+  s.DD[P1] = dd;
+  s.D2[P0] = d2;
+  s.Uh[P1] = uh;
+  s.Dh[P0] = dh;
+  return out;
+}
+
+template <int K>
+__device__ __forceinline__ float step1(Line1& s, float u, float a, float nb, float c, float eta) {
+  constexpr int P0 = K & 1, P1 = (K + 1) & 1;
+  const float d = u - s.Up;
+  const float uh = fmaf(c, s.Up, fmaf(a, d, nb * s.D[P0]));
+  const float dd = d - s.D[P0];
+  const float d2 = dd - s.DD[P0];
+  const float dh = uh - s.Uh[P0];
+  const float A = limit(eta * fmaf(-0.125f, s.D2[P1], s.Dh[P1]), dh, s.Dh[P0]);
+  const float out = s.Uh[P1] - (A - s.A);
+  s.A = A;
+  s.Up = u;
+  s.D[P1] = d;
+  s.DD[P1] = dd;
+  s.D2[P0] = d2;
+  s.Uh[P1] = uh;
+  s.Dh[P0] = dh;
+  return out;
+}
+
+__device__ __forceinline__ void init2(Line2& s, f2 u0) {
+  const f2 z = pk(0.0f, 0.0f);
+  s.Up = u0;
+  s.A = z;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) s.D[k] = s.DD[k] = s.D2[k] = s.Uh[k] = s.Dh[k] = z;
+}
+__device__ __forceinline__ void init1(Line1& s) {
+  s.Up = s.A = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) s.D[k] = s.DD[k] = s.D2[k] = s.Uh[k] = s.Dh[k] = 0.0f;
+}
+
+// Transport coefficients of cell k-1 from w_{k-1}, w_k and Q+_{k-2}:
+// Q+ of Eq. shasta-diff and Q-_{k-1} = 1 - Q+_{k-2}.
+__device__ __forceinline__ void coeffs(float tau, float w1, float w0, float& qprev, float& a,
+                                       float& nb, float& c) {
+  const float e1 = tau * w1, e0 = tau * w0;
+  const float qp = __fdividef(0.5f - e1, 1.0f + (e0 - e1));
+  const float qm = 1.0f - qprev;
+  qprev = qp;
+  a = 0.5f * qp * qp;
+  nb = -0.5f * qm * qm;
+  c = qp + qm;
+}
+
+// ------------------------------------------------------------- kernel ----
+//
+// Pipeline (q = newest loaded position; lag 7):
+//   U^n_q read; (w, p)^n_q and (w, p)^h_{q-4} recovered together (packed)
+//   half-step pass of (E, M) with newest cell q      -> U^h_{q-3}
+//   full-step pass of (E, M, R) with newest cell q-4 -> U^{n+1}_{q-7}
+
 template <int EOS, int AXIS, bool MIXED, int WARPS, int RING, int DIST, int MINB>
 __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParams P) {
   constexpr bool XP = AXIS == 0;
-  static_assert(RING >= DIST + 4 && (RING & (RING - 1)) == 0, "ring too small");
+  constexpr int LAG = 7;
+  static_assert(RING == 8 && DIST == 3, "ring layout assumes 8 slots, 3 ahead");
   extern __shared__ __align__(16) float smem[];
 
   const int lane = threadIdx.x & 31;
@@ -218,14 +458,14 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParam
   const int s1 = min(s0 + P.seg_len, n);
   // positions streamed: qs .. qe (the x path starts on a chunk boundary)
   const int qs = XP ? ((s0 - 2 * NG) & ~(CH - 1)) : s0 - 2 * NG;
-  const int qe = s1 + 2 * NG - 1;
-  const int trip = ((qe - qs + 1) + 3) & ~3;
-  // steady iterations [i1, i2): every position they touch is inside [0, n)
-  // (reads q and q-3, frozen override at q-3, prefetch ahead, store q-6)
+  const int qe = s1 + LAG - 1;
+  const int trip = ((qe - qs + 1) + 7) & ~7;
+  // steady blocks [i1, i2): every position they touch is inside [0, n)
+  // (reads q, q-3 and q-4, prefetch ahead, store q-7)
   const int ahead = XP ? 2 * CH : DIST;
-  int i1 = (3 - qs) > 0 ? ((3 - qs) + 3) & ~3 : 0;
-  int i2 = ((n - 1 - ahead) - qs + 1);
-  i2 = i2 > 0 ? (i2 & ~3) : 0;
+  int i1 = (4 - qs) > 0 ? ((4 - qs) + 7) & ~7 : 0;
+  int i2 = (n - 1 - ahead) - qs + 1;
+  i2 = i2 > 0 ? (i2 & ~7) : 0;
   i2 = i2 < trip ? i2 : trip;
   if (i2 < i1) i2 = i1;
 
@@ -233,14 +473,17 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParam
   float* out0 = static_cast<float*>(P.out[0]);
   const long long fs = P.fstride;
   const float tau_h = float(P.tau_h), tau_f = float(P.tau_f);
-  const float htau_h = float(P.htau_h), htau_f = float(P.htau_f);
   const float eta = float(P.eta);
   const float omd = float(P.omd), B = float(P.bag_B), ec = float(P.bag_ec);
+  const f2 omd2 = pk(omd, omd);
+  const f2 eta2 = pk(eta, eta), m8c = pk(-0.125f, -0.125f);
+  const f2 ht_h = pk(float(P.htau_h), float(P.htau_h));
+  const f2 ht_f = pk(float(P.htau_f), float(P.htau_f));
   const bool frozen = P.bc == BC_FROZEN;
   unsigned nclamp = 0;
 
+  auto x_slot = [&](int C) -> float* { return wsm + ((C + 3 * 4) % XSLOTS) * XSLOT; };
   // x path: cooperative copy of chunk C = positions [8C, 8C+8) of 32 rows
-  auto x_slot = [&](int C) -> float* { return wsm + ((C + 3 * 4) % XSLOTS) * (NF * LANES * XSTR); };
   auto x_issue = [&](int C, bool ghost) {
     float* ring = x_slot(C);
     const int r0 = lane >> 3, pc = lane & 7;
@@ -253,31 +496,30 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParam
       if (ghost) {
 #pragma unroll
         for (int f = 0; f < NF; ++f)
-          cp_async4(ring + (f * LANES + row) * XSTR + pc, src_addr<AXIS>(P, f, tr * P.sb, tr, pos, n));
+          cp_async4(ring + ring_off<true>(f, row, pc), src_addr<AXIS>(P, f, tr * P.sb, tr, pos, n));
       } else {
         const float* rp = in0 + tr * P.sb + pos;
 #pragma unroll
-        for (int f = 0; f < NF; ++f)
-          cp_async4(ring + (f * LANES + row) * XSTR + pc, rp + gfield<AXIS>(f) * fs);
+        for (int f = 0; f < NF; ++f) cp_async4(ring + ring_off<true>(f, row, pc), rp + gfield<AXIS>(f) * fs);
       }
     }
   };
-  // y/z path: own-lane copy of position q
-  auto yz_issue = [&](int q, bool ghost) {
-    float* ring = wsm + ((q - qs) & (RING - 1)) * (NF * LANES) + lane;
+  // y/z path: own-lane copy of position q into ring slot `slot`
+  auto yz_issue = [&](float* slot, int q, bool ghost) {
     if (ghost) {
 #pragma unroll
-      for (int f = 0; f < NF; ++f) cp_async4(ring + f * LANES, src_addr<AXIS>(P, f, base, tl, q, n));
+      for (int f = 0; f < NF; ++f)
+        cp_async4(slot + ring_off<false>(f, lane, 0), src_addr<AXIS>(P, f, base, tl, q, n));
     } else {
       const float* rp = in0 + base + (long long)q * P.stride;
 #pragma unroll
-      for (int f = 0; f < NF; ++f) cp_async4(ring + f * LANES, rp + gfield<AXIS>(f) * fs);
+      for (int f = 0; f < NF; ++f) cp_async4(slot + ring_off<false>(f, lane, 0), rp + gfield<AXIS>(f) * fs);
     }
   };
-  auto at = [&](int q, int f) -> float& {
-    if (XP) return x_slot(q >> 3)[(f * LANES + lane) * XSTR + (q & 7)];
-    return wsm[((q - qs) & (RING - 1)) * (NF * LANES) + f * LANES + lane];
+  auto rd2 = [&](const float* slot, int pos, int p) -> f2 {
+    return *reinterpret_cast<const f2*>(slot + ring_off<XP>(2 * p, lane, pos));
   };
+  auto rdR = [&](const float* slot, int pos) -> float { return slot[ring_off<XP>(4, lane, pos)]; };
 
   // prologue
   if (XP) {
@@ -286,162 +528,178 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParam
   } else {
 #pragma unroll 1
     for (int d = 0; d < DIST; ++d) {
-      if (qs + d <= qe) yz_issue(qs + d, true);
+      if (qs + d <= qe) yz_issue(wsm + d * YSLOT, qs + d, true);
       cp_commit();
     }
   }
 
-  // register windows, slot = (position - qs) & 3
-  float Uh_prev[4];     // U^n_{q-1}: E, M_par, M_t1, M_t2
-  float dn[4][4];       // Delta^n_j, j = q-4 .. q-1 (E, M)
-  float wn[4], pn[4];   // (w, p)^n at q-3 .. q
-  float uh[4][4];       // Uhat^h_j, j = q-4 .. q-1 (E, M)
-  float ah[4];          // A^h_{q-4}
-  float Uf_prev[NF];    // U^n_{q-4}
-  float df[4][NF];      // Delta^n_j, j = q-7 .. q-4
-  float wh[4], ph[4];   // (w, p)^h at q-6 .. q-3
-  float uf[4][NF];      // Uhat^f_j, j = q-7 .. q-4
-  float af[NF];         // A^f_{q-7}
-  float qph = 0.5f, qpf = 0.5f;  // Q+ of the previous cell, half and full step
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    Uh_prev[k] = k == 0 ? 1.0f : 0.0f;
-    ah[k] = 0.0f;
-    wn[k] = pn[k] = wh[k] = ph[k] = 0.0f;
-#pragma unroll
-    for (int s = 0; s < 4; ++s) dn[s][k] = uh[s][k] = 0.0f;
-  }
-#pragma unroll
-  for (int f = 0; f < NF; ++f) {
-    Uf_prev[f] = f == 0 ? 1.0f : 0.0f;
-    af[f] = 0.0f;
-#pragma unroll
-    for (int s = 0; s < 4; ++s) df[s][f] = uf[s][f] = 0.0f;
-  }
+  // per-line state: pairs A = (E, M_par), B = (M_t1, M_t2)
+  Line2 hA, hB, fA, fB;  // half-step and full-step passes
+  Line1 fR;              // full-step pass of R
+  init2(hA, pk(1.0f, 0.0f));
+  init2(hB, pk(0.0f, 0.0f));
+  init2(fA, pk(1.0f, 0.0f));
+  init2(fB, pk(0.0f, 0.0f));
+  init1(fR);
+  f2 HA = pk(1.0f, 0.0f), HB = pk(0.0f, 0.0f);  // U^h_{q-4}, recovered next step
+  float wn1 = 0.0f, wh1 = 0.0f;                 // w^n_{q-1}, w^h_{q-5}
+  f2 fn[2], fh[2];                               // (p w, p) by parity
+  fn[0] = fn[1] = fh[0] = fh[1] = pk(0.0f, 0.0f);
+  float qph = 0.5f, qpf = 0.5f;                 // Q+ of the previous cell
 
-  // One streaming step at position q = qs + i0 + K.  GH: positions outside
-  // [0, n) may be touched (boundary rule, frozen ghosts, segment edges).
-  auto body = [&](int i0, auto Kc, auto Gc) {
+  // One streaming step at position q = qs + i + K (K = parity of q - qs).
+  //   sq, sq4: ring slots of positions q and q-4; pq, pq4: their chunk
+  //   offsets (x path); sjo: slot of output position q-7 (x path); siss:
+  //   slot receiving position q + DIST (y/z path).
+  auto body = [&](int i, auto Kc, auto Gc, const float* sq, const float* sq4, float* sjo,
+                  float* siss) {
     constexpr int K = decltype(Kc)::value;
     constexpr bool GH = decltype(Gc)::value;
-    const int q = qs + i0 + K;
-#define SL(o) ((K - (o) + 16) & 3)
-    // ---- staging: make position q resident, prefetch ahead
-    if (XP) {
-      if ((q & 7) == 0) {
-        cp_wait<0>();
-        __syncwarp();
-        if (GH) {
-          if ((q >> 3) + 1 <= (qe >> 3)) x_issue((q >> 3) + 1, true);
-        } else {
-          x_issue((q >> 3) + 1, false);
-        }
-        cp_commit();
-      }
-    } else {
-      cp_wait<DIST - 1>();
-    }
-    // ---- stage 0: U^n_q (E, M), recovery at level n
-    float uq[4];
-#pragma unroll
-    for (int f = 0; f < 4; ++f) uq[f] = at(q, f);
-    if (GH && flips(q, n, P.bc)) uq[1] = -uq[1];
+    constexpr int P0 = K & 1;
+    const int q = qs + i + K;
+    const int pq = XP ? (q & 7) : 0;
+    const int pq4 = XP ? ((q - 4) & 7) : 0;
+    if (!XP) cp_wait<DIST - 1>();
+    // ---- U^n_q (E, M)
+    f2 uA = rd2(sq, pq, 0);
+    const f2 uB = rd2(sq, pq, 1);
+    if (GH && flips(q, n, P.bc)) uA = neg_hi(uA);
     if (!XP) {
       if (GH) {
-        if (q + DIST <= qe) yz_issue(q + DIST, true);
+        if (q + DIST <= qe) yz_issue(siss, q + DIST, true);
       } else {
-        yz_issue(q + DIST, false);
+        yz_issue(siss, q + DIST, false);
       }
       cp_commit();
     }
+    // ---- recovery of U^n_q (lo) and U^h_{q-4} (hi) together
+    float wn0, wh0;
+    f2 fn0, fh0;
     {
-      float w, p;
-      const unsigned c0 = rec32<EOS, MIXED>(uq[0], uq[1], uq[2], uq[3], omd, B, ec, w, p);
-      nclamp += (q >= s0 && q < s1) ? c0 : 0u;
-      wn[SL(0)] = w;
-      pn[SL(0)] = p;
+      float E0, m10, m20, m30, E1, m11, m21, m31;
+      up(uA, E0, m10);
+      up(uB, m20, m30);
+      up(HA, E1, m11);
+      up(HB, m21, m31);
+      f2 w2, p2;
+      const unsigned c0 = rec2<EOS, MIXED>(pk(E0, E1), pk(m10, m11), pk(m20, m21), pk(m30, m31),
+                                           omd2, omd, B, ec, w2, p2);
+      nclamp += ((unsigned)(q - s0) < (unsigned)(s1 - s0)) ? c0 : 0u;
+      float pl, phi, pwl, pwh;
+      up(w2, wn0, wh0);
+      up(p2, pl, phi);
+      up(mul2(p2, w2), pwl, pwh);
+      fn0 = pk(pwl, pl);
+      fh0 = pk(pwh, phi);
     }
-    // ---- stage 1: half-step transported value at q-1 (E, M only)
+    // ---- half-step pass, newest cell q: U^h_{q-3}
     {
-      const float e1 = tau_h * wn[SL(1)], e0 = tau_h * wn[SL(0)];
-      const float qp = __fdividef(0.5f - e1, 1.0f + (e0 - e1));  // Q+_{q-1}
-      const float qm = 1.0f - qph;                                // Q-_{q-1}
-      qph = qp;
-      const float a = 0.5f * qp * qp, b = 0.5f * qm * qm, c = qp + qm;
-#pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        const float d = uq[f] - Uh_prev[f];  // Delta_{q-1}
-        uh[SL(1)][f] = fmaf(c, Uh_prev[f], fmaf(a, d, -b * dn[SL(2)][f]));
-        dn[SL(1)][f] = d;
-        Uh_prev[f] = uq[f];
+      float a, nb, c;
+      coeffs(tau_h, wn1, wn0, qph, a, nb, c);
+      const f2 src = mul2(ht_h, sub2(fn[P0], fn0));  // f_{q-2} - f_q
+      fn[P0] = fn0;
+      wn1 = wn0;
+      const f2 a2 = pk(a, a), nb2 = pk(nb, nb), c2 = pk(c, c);
+      HA = step2<K, true>(hA, uA, a2, nb2, c2, src, eta2, m8c);
+      HB = step2<K, false>(hB, uB, a2, nb2, c2, src, eta2, m8c);
+      if (GH && frozen && (q - NG < 0 || q - NG >= n)) {
+        // frozen ghost: the half-step state is the stored ghost value
+        const float* s3 = XP ? x_slot((q - NG) >> 3) : wsm + ((q - NG - qs) & (RING - 1)) * YSLOT;
+        const int p3 = XP ? ((q - NG) & 7) : 0;
+        HA = rd2(s3, p3, 0);
+        HB = rd2(s3, p3, 1);
       }
-      uh[SL(1)][0] += htau_h * (pn[SL(2)] * wn[SL(2)] - pn[SL(0)] * wn[SL(0)]);
-      uh[SL(1)][1] += htau_h * (pn[SL(2)] - pn[SL(0)]);
     }
-    // ---- stage 2: half-step flux at q-3, state U^h_{q-3}
-    float hs[4];
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      const float an = afx(uh[SL(4)][f], uh[SL(3)][f], uh[SL(2)][f], uh[SL(1)][f], dn[SL(4)][f],
-                           dn[SL(3)][f], dn[SL(2)][f], eta);
-      hs[f] = uh[SL(3)][f] - (an - ah[f]);
-      ah[f] = an;
-    }
-    if (GH && frozen && (q - NG < 0 || q - NG >= n)) {
-#pragma unroll
-      for (int f = 0; f < 4; ++f) hs[f] = at(q - NG, f);
-    }
-    // ---- stage 3: recovery at n+1/2, position q-3
+    // ---- full-step pass, newest cell q-4 (old state re-read): U^{n+1}_{q-7}
+    f2 oA, oB;
+    float oR;
     {
-      float w, p;
-      const unsigned c3 = rec32<EOS, MIXED>(hs[0], hs[1], hs[2], hs[3], omd, B, ec, w, p);
-      nclamp += (q - NG >= s0 && q - NG < s1) ? c3 : 0u;
-      wh[SL(3)] = w;
-      ph[SL(3)] = p;
+      f2 vA = rd2(sq4, pq4, 0);
+      const f2 vB = rd2(sq4, pq4, 1);
+      const float vR = rdR(sq4, pq4);
+      if (GH && flips(q - 4, n, P.bc)) vA = neg_hi(vA);
+      float a, nb, c;
+      coeffs(tau_f, wh1, wh0, qpf, a, nb, c);
+      const f2 src = mul2(ht_f, sub2(fh[P0], fh0));  // f_{q-6} - f_{q-4}
+      fh[P0] = fh0;
+      wh1 = wh0;
+      const f2 a2 = pk(a, a), nb2 = pk(nb, nb), c2 = pk(c, c);
+      oA = step2<K, true>(fA, vA, a2, nb2, c2, src, eta2, m8c);
+      oB = step2<K, false>(fB, vB, a2, nb2, c2, src, eta2, m8c);
+      oR = step1<K>(fR, vR, a, nb, c, eta);
     }
-    // ---- stage 4: full-step transported value at q-4 from U^n
-    {
-      float u3[NF];
-#pragma unroll
-      for (int f = 0; f < NF; ++f) u3[f] = at(q - 3, f);
-      if (GH && flips(q - 3, n, P.bc)) u3[1] = -u3[1];
-      const float e4 = tau_f * wh[SL(4)], e3 = tau_f * wh[SL(3)];
-      const float qp = __fdividef(0.5f - e4, 1.0f + (e3 - e4));  // Q+_{q-4}
-      const float qm = 1.0f - qpf;
-      qpf = qp;
-      const float a = 0.5f * qp * qp, b = 0.5f * qm * qm, c = qp + qm;
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        const float d = u3[f] - Uf_prev[f];  // Delta_{q-4}
-        uf[SL(4)][f] = fmaf(c, Uf_prev[f], fmaf(a, d, -b * df[SL(5)][f]));
-        df[SL(4)][f] = d;
-        Uf_prev[f] = u3[f];
-      }
-      uf[SL(4)][0] += htau_f * (ph[SL(5)] * wh[SL(5)] - ph[SL(3)] * wh[SL(3)]);
-      uf[SL(4)][1] += htau_f * (ph[SL(5)] - ph[SL(3)]);
-    }
-    // ---- stage 5: full-step flux at q-6, new state U^{n+1}_{q-6}
-    float ov[NF];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      const float an = afx(uf[SL(7)][f], uf[SL(6)][f], uf[SL(5)][f], uf[SL(4)][f], df[SL(7)][f],
-                           df[SL(6)][f], df[SL(5)][f], eta);
-      ov[f] = uf[SL(6)][f] - (an - af[f]);
-      af[f] = an;
-    }
-    const int jo = q - 2 * NG;
+    const int jo = q - LAG;
     if (XP) {
       // the ring entry of position jo is dead: stage the result there
       if (jo >= s0 && jo < s1) {
-#pragma unroll
-        for (int f = 0; f < NF; ++f) at(jo, f) = ov[f];
+        const int pj = jo & 7;
+        *reinterpret_cast<f2*>(sjo + ring_off<true>(0, lane, pj)) = oA;
+        *reinterpret_cast<f2*>(sjo + ring_off<true>(2, lane, pj)) = oB;
+        sjo[ring_off<true>(4, lane, pj)] = oR;
       }
-      if (jo >= s0 && ((jo & 7) == 7 || jo == s1 - 1)) {
+    } else if (valid && jo >= s0 && jo < s1) {
+      float* op = out0 + base + (long long)jo * P.stride;
+      float o0, o1, o2, o3;
+      up(oA, o0, o1);
+      up(oB, o2, o3);
+      op[gfield<AXIS>(0) * fs] = o0;
+      op[gfield<AXIS>(1) * fs] = o1;
+      op[gfield<AXIS>(2) * fs] = o2;
+      op[gfield<AXIS>(3) * fs] = o3;
+      op[gfield<AXIS>(4) * fs] = oR;
+    }
+  };
+
+  // two steps: positions qs+i and qs+i+1 (i even)
+  auto duo = [&](int i, auto Gc) {
+    if (XP) {
+      const int C = (qs + i) >> 3;  // chunk of both positions
+      float* pC = x_slot(C);
+      float* pCm = x_slot(C - 1);
+      const float* s4 = ((qs + i) & 4) ? pC : pCm;  // chunk of positions q-4
+      body(i, ic<0>{}, Gc, pC, s4, pCm, nullptr);
+      body(i, ic<1>{}, Gc, pC, s4, ((qs + i + 1) & 7) == 7 ? pC : pCm, nullptr);
+    } else {
+      const int r = i & 7;  // ring slot of position qs+i
+      float* yb = wsm + r * YSLOT;
+      float* yb4 = wsm + (r ^ 4) * YSLOT;
+      body(i, ic<0>{}, Gc, yb, yb4, nullptr, wsm + ((r + 3) & 7) * YSLOT);
+      body(i, ic<1>{}, Gc, yb + YSLOT, yb4 + YSLOT, nullptr, wsm + ((r + 4) & 7) * YSLOT);
+    }
+  };
+
+  int fl = s0;  // x path: next output position to write back
+#pragma unroll 1
+  for (int i0 = 0; i0 < trip; i0 += 8) {
+    const bool steady = i0 >= i1 && i0 + 8 <= i2;
+    if (XP) {
+      // chunk (qs + i0) / 8 becomes resident; prefetch the next one
+      const int C = (qs + i0) >> 3;
+      cp_wait<0>();
+      __syncwarp();
+      if (steady)
+        x_issue(C + 1, false);
+      else if (C + 1 <= (qe >> 3))
+        x_issue(C + 1, true);
+      cp_commit();
+    }
+#pragma unroll 1
+    for (int h = 0; h < 8; h += 2) {
+      if (steady)
+        duo(i0 + h, bc_<false>{});
+      else
+        duo(i0 + h, bc_<true>{});
+    }
+    if (XP) {
+      // write back completed output chunks (positions [fl, avail))
+      const int avail = min(qs + i0 + 8 - LAG, s1);
+#pragma unroll 1
+      while (fl < s1 && (avail - fl >= CH || avail == s1)) {
         __syncwarp();
-        const float* ring = x_slot(jo >> 3);
+        const float* ring = x_slot(fl >> 3);
         const int r0 = lane >> 3, pc = lane & 7;
-        const int pos = (jo & ~7) + pc;
-        if (pos >= s0 && pos <= jo) {
+        const int pos = fl + pc;
+        if (pos < avail) {
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
             const int row = r0 + 4 * k;
@@ -449,32 +707,13 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParam
             if (tr < P.plane) {
               float* op = out0 + tr * P.sb + pos;
 #pragma unroll
-              for (int f = 0; f < NF; ++f) op[gfield<AXIS>(f) * fs] = ring[(f * LANES + row) * XSTR + pc];
+              for (int f = 0; f < NF; ++f) op[gfield<AXIS>(f) * fs] = ring[ring_off<true>(f, row, pc)];
             }
           }
         }
         __syncwarp();
+        fl = min(fl + CH, s1);
       }
-    } else if (valid && jo >= s0 && jo < s1) {
-      float* op = out0 + base + (long long)jo * P.stride;
-#pragma unroll
-      for (int f = 0; f < NF; ++f) op[gfield<AXIS>(f) * fs] = ov[f];
-    }
-#undef SL
-  };
-
-#pragma unroll 1
-  for (int i0 = 0; i0 < trip; i0 += 4) {
-    if (i0 >= i1 && i0 < i2) {
-      body(i0, ic<0>{}, bc_<false>{});
-      body(i0, ic<1>{}, bc_<false>{});
-      body(i0, ic<2>{}, bc_<false>{});
-      body(i0, ic<3>{}, bc_<false>{});
-    } else {
-      body(i0, ic<0>{}, bc_<true>{});
-      body(i0, ic<1>{}, bc_<true>{});
-      body(i0, ic<2>{}, bc_<true>{});
-      body(i0, ic<3>{}, bc_<true>{});
     }
   }
   cp_wait<0>();
