@@ -33,8 +33,10 @@ struct shasta_ctx {
   shasta_opts o{};
   int is32 = 1;
   size_t ncell = 0, esize = 4;
-  void* state_mem = nullptr;  // both buffers, 10 fields
-  void* buf[2][NF] = {};
+  void* state_mem = nullptr;  // both buffers
+  FieldView view[2] = {};     // where the fields of each buffer live
+  float* quad[2] = {};        // FP32 / MIXED: (E, Mx, My, Mz) per cell
+  float* rf[2] = {};          // FP32 / MIXED: R
   int cur = 0;
   bool state_set = false;
   void* frozen = nullptr;
@@ -141,9 +143,8 @@ shasta_status check_count(shasta_ctx* c, bool prims, const double* const f[5]) {
 
 shasta_status after_set(shasta_ctx* c) {
   if (c->g.bc == SHASTA_BC_FROZEN) {
-    const void* f[5];
-    for (int k = 0; k < 5; ++k) f[k] = c->buf[c->cur][k];
-    CK(launch_frozen_capture(f, c->frozen, c->g.nx, c->g.ny, c->g.nz, c->is32, c->stream),
+    CK(launch_frozen_capture(c->view[c->cur], c->frozen, c->g.nx, c->g.ny, c->g.nz, c->is32,
+                             c->stream),
        "frozen_capture");
   }
   CK(cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), c->stream), "memset");
@@ -157,9 +158,13 @@ SweepParams sweep_params(shasta_ctx* c, int axis, int from) {
   memset(&P, 0, sizeof P);
   long long nx = c->g.nx, ny = c->g.ny, nz = c->g.nz;
   for (int k = 0; k < NF; ++k) {
-    P.in[k] = c->buf[from][k];
-    P.out[k] = c->buf[from ^ 1][k];
+    P.in[k] = c->view[from].p[k];
+    P.out[k] = c->view[from ^ 1].p[k];
   }
+  P.qin = c->quad[from];
+  P.rin = c->rf[from];
+  P.qout = c->quad[from ^ 1];
+  P.rout = c->rf[from ^ 1];
   if (axis == 0) {
     P.n = (int)nx;
     P.stride = 1;
@@ -195,23 +200,32 @@ SweepParams sweep_params(shasta_ctx* c, int axis, int from) {
   P.bag_B = c->eos.B;
   P.bag_ec = c->eos.e_c;
   P.clamp_count = c->d_count;
-  // Lines are cut into segments until the launch has about warps_per_sm
-  // warps per SM (each segment re-reads a 6-cell halo per side).
+  // Lines are cut into segments (each re-reads a 6-cell halo per side and
+  // pays a 7-cell pipeline lag).  One wave of resident warps loops over the
+  // (line group, segment) items; the segment count minimises
+  // ceil(items / resident warps) * (segment length + 13).
   int nseg = 1;
   if (c->o.precision != SHASTA_FP64) {
     const long long groups = (P.plane + 31) / 32;
-    const long long target = (long long)c->sm_count * c->warps_per_sm;
-    nseg = (int)((target + groups - 1) / groups);
-    const int max_seg = P.n / 32 > 1 ? P.n / 32 : 1;
-    if (nseg > max_seg) nseg = max_seg;
+    int wpsm = c->o.precision == SHASTA_MIXED ? sweep_warps_per_sm_mixed(axis, c->variant)
+                                              : sweep_warps_per_sm_f32(axis, c->variant);
+    if (wpsm < 1) wpsm = 1;
+    const long long slots = (long long)c->sm_count * wpsm;
+    double best = 1e300;
+    const int max_seg = P.n / 16 > 1 ? P.n / 16 : 1;
+    for (int k = 1; k <= max_seg && k <= 16; ++k) {
+      const long long items = groups * k;
+      const long long waves = (items + slots - 1) / slots;
+      const double cost = (double)waves * ((double)P.n / k + 13.0);
+      if (cost < best * 0.999) {
+        best = cost;
+        nseg = k;
+      }
+    }
     if (c->force_nseg > 0) nseg = c->force_nseg;
-    if (nseg < 1) nseg = 1;
   }
-  int seg = (P.n + nseg - 1) / nseg;
-  seg = (seg + 7) & ~7;
-  P.seg_len = seg;
-  P.nseg = (P.n + seg - 1) / seg;
-  P.fstride = (long long)((char*)c->buf[0][1] - (char*)c->buf[0][0]) / (long long)c->esize;
+  P.seg_len = (P.n + nseg - 1) / nseg;
+  P.nseg = nseg;
   P.variant = c->variant;
   return P;
 }
@@ -329,12 +343,30 @@ shasta_status shasta_create(const shasta_grid* g, double dx, double lambda, cons
     release(c);
     return fail(nullptr, err == cudaErrorMemoryAllocation ? SHASTA_ENOMEM : SHASTA_ECUDA, m);
   };
-  // 10 fields, each padded to 256 bytes
+  // FP64: five dense fields per buffer.  FP32 / MIXED: a quad array of
+  // (E, Mx, My, Mz) per cell and a dense R array per buffer.  Every array
+  // starts on a 256-byte boundary.
   size_t field_bytes = ((c->ncell * c->esize + 255) / 256) * 256;
   cudaError_t err = cudaMalloc(&c->state_mem, 2 * NF * field_bytes);
   if (err != cudaSuccess) return bail(err, "cudaMalloc state");
-  for (int b = 0; b < 2; ++b)
-    for (int k = 0; k < NF; ++k) c->buf[b][k] = (char*)c->state_mem + (b * NF + k) * field_bytes;
+  for (int b = 0; b < 2; ++b) {
+    char* bb = (char*)c->state_mem + (size_t)b * NF * field_bytes;
+    if (c->is32) {
+      c->quad[b] = (float*)bb;
+      c->rf[b] = (float*)(bb + 4 * field_bytes);
+      for (int k = 0; k < 4; ++k) {
+        c->view[b].p[k] = c->quad[b] + k;
+        c->view[b].s[k] = 4;
+      }
+      c->view[b].p[4] = c->rf[b];
+      c->view[b].s[4] = 1;
+    } else {
+      for (int k = 0; k < NF; ++k) {
+        c->view[b].p[k] = bb + (size_t)k * field_bytes;
+        c->view[b].s[k] = 1;
+      }
+    }
+  }
   if (g->bc == SHASTA_BC_FROZEN) {
     err = cudaMalloc(&c->frozen, frozen_elems(g->nx, g->ny, g->nz) * c->esize);
     if (err != cudaSuccess) return bail(err, "cudaMalloc frozen");
@@ -383,7 +415,8 @@ shasta_status shasta_set_conserved(shasta_ctx* c, const double* E, const double*
   }
   c->cur = 0;
   for (int k = 0; k < 5; ++k)
-    CK(launch_from_f64(d[k], c->buf[0][k], c->ncell, c->is32, c->stream), "convert in");
+    CK(launch_from_f64(d[k], c->view[0].p[k], c->view[0].s[k], c->ncell, c->is32, c->stream),
+       "convert in");
   return after_set(c);
 }
 
@@ -402,9 +435,7 @@ shasta_status shasta_set_primitives(shasta_ctx* c, const double* e, const double
     if (s != SHASTA_OK) return s;
   }
   c->cur = 0;
-  void* out[5];
-  for (int k = 0; k < 5; ++k) out[k] = c->buf[0][k];
-  CK(launch_prim2cons(d, out, c->ncell, c->is32, eos_params(c), c->stream), "prim2cons");
+  CK(launch_prim2cons(d, c->view[0], c->ncell, c->is32, eos_params(c), c->stream), "prim2cons");
   return after_set(c);
 }
 
@@ -451,7 +482,9 @@ shasta_status shasta_get_conserved(shasta_ctx* c, double* E, double* Mx, double*
   for (int k = 0; k < 5; ++k) {
     if (!dst[k]) continue;
     double* d = mem == SHASTA_MEM_DEVICE ? dst[k] : c->staging + (size_t)k * c->ncell;
-    CK(launch_to_f64(c->buf[c->cur][k], d, c->ncell, c->is32, c->stream), "convert out");
+    CK(launch_to_f64(c->view[c->cur].p[k], c->view[c->cur].s[k], d, c->ncell, c->is32,
+                     c->stream),
+       "convert out");
     if (mem == SHASTA_MEM_HOST)
       CK(cudaMemcpyAsync(dst[k], d, c->ncell * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
          "cudaMemcpyAsync D2H");
@@ -474,9 +507,7 @@ shasta_status shasta_get_primitives(shasta_ctx* c, double* e, double* vx, double
   }
   for (int k = 0; k < 6; ++k)
     d[k] = !dst[k] ? nullptr : (mem == SHASTA_MEM_DEVICE ? dst[k] : c->staging + (size_t)k * c->ncell);
-  const void* in[5];
-  for (int k = 0; k < 5; ++k) in[k] = c->buf[c->cur][k];
-  CK(launch_recover(in, d, c->ncell, c->is32, eos_params(c), c->stream), "recover");
+  CK(launch_recover(c->view[c->cur], d, c->ncell, c->is32, eos_params(c), c->stream), "recover");
   if (mem == SHASTA_MEM_HOST)
     for (int k = 0; k < 6; ++k)
       if (dst[k])
@@ -491,9 +522,8 @@ shasta_status shasta_totals(shasta_ctx* c, double out[5]) {
   if (!c || !out) return SHASTA_EINVAL;
   if (!c->state_set) return fail(c, SHASTA_EINVAL, "state not set");
   DeviceGuard dg(c->device);
-  const void* f[5];
-  for (int k = 0; k < 5; ++k) f[k] = c->buf[c->cur][k];
-  CK(launch_totals(f, c->ncell, c->is32, c->partials, c->d_tot, c->stream), "totals");
+  CK(launch_totals(c->view[c->cur], c->ncell, c->is32, c->partials, c->d_tot, c->stream),
+     "totals");
   CK(cudaMemcpyAsync(c->h_small, c->d_tot, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
      "memcpy totals");
   CK(cudaStreamSynchronize(c->stream), "sync");

@@ -18,17 +18,24 @@ inline unsigned grid_for(size_t n) {
 }
 
 template <class T>
-__global__ void k_from_f64(const double* __restrict__ src, T* __restrict__ dst, size_t n) {
+__global__ void k_from_f64(const double* __restrict__ src, T* __restrict__ dst, long long ds,
+                           size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x)
-    dst[i] = T(src[i]);
+    dst[i * ds] = T(src[i]);
 }
 
 template <class T>
-__global__ void k_to_f64(const T* __restrict__ src, double* __restrict__ dst, size_t n) {
+__global__ void k_to_f64(const T* __restrict__ src, long long ss, double* __restrict__ dst,
+                         size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x)
-    dst[i] = double(src[i]);
+    dst[i] = double(src[i * ss]);
+}
+
+template <class T>
+__device__ __forceinline__ T& fv(const FieldView& v, int k, size_t i) {
+  return static_cast<T*>(v.p[k])[(long long)i * v.s[k]];
 }
 
 __device__ __forceinline__ double eos_p(const EosParams& q, double e) {
@@ -38,7 +45,7 @@ __device__ __forceinline__ double eos_p(const EosParams& q, double e) {
 
 struct Ptr5 {
   const double* in[5];
-  void* out[5];
+  FieldView out;
 };
 
 // Sec. 2: R = n gamma, M = (e + p) gamma^2 v, E = (e + p) gamma^2 - p.
@@ -51,16 +58,16 @@ __global__ void k_prim2cons(Ptr5 p, size_t n, EosParams q) {
     double g2 = 1.0 / (1.0 - v2);
     double pr = eos_p(q, e);
     double w = (e + pr) * g2;
-    static_cast<T*>(p.out[0])[i] = T(w - pr);
-    static_cast<T*>(p.out[1])[i] = T(w * vx);
-    static_cast<T*>(p.out[2])[i] = T(w * vy);
-    static_cast<T*>(p.out[3])[i] = T(w * vz);
-    static_cast<T*>(p.out[4])[i] = T(nb * sqrt(g2));
+    fv<T>(p.out, 0, i) = T(w - pr);
+    fv<T>(p.out, 1, i) = T(w * vx);
+    fv<T>(p.out, 2, i) = T(w * vy);
+    fv<T>(p.out, 3, i) = T(w * vz);
+    fv<T>(p.out, 4, i) = T(nb * sqrt(g2));
   }
 }
 
 struct Rec6 {
-  const void* in[5];
+  FieldView in;
   double* out[6];
 };
 
@@ -69,11 +76,10 @@ template <class T>
 __global__ void k_recover(Rec6 r, size_t n, EosParams q) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {
-    double E = double(static_cast<const T*>(r.in[0])[i]);
-    double m[3] = {double(static_cast<const T*>(r.in[1])[i]),
-                   double(static_cast<const T*>(r.in[2])[i]),
-                   double(static_cast<const T*>(r.in[3])[i])};
-    double R = double(static_cast<const T*>(r.in[4])[i]);
+    double E = double(fv<T>(r.in, 0, i));
+    double m[3] = {double(fv<T>(r.in, 1, i)), double(fv<T>(r.in, 2, i)),
+                   double(fv<T>(r.in, 3, i))};
+    double R = double(fv<T>(r.in, 4, i));
     double e = 0.0, v[3] = {0.0, 0.0, 0.0}, nb = 0.0, pp = 0.0;
     if (E > 0.0) {
       double M = sqrt((m[0] * m[0] + m[1] * m[1]) + m[2] * m[2]);
@@ -137,7 +143,7 @@ constexpr int kTotThreads = 256;
 constexpr int kTotMaxBlocks = 1024;
 
 struct Tot5 {
-  const void* f[5];
+  FieldView f;
 };
 
 template <class T>
@@ -149,7 +155,7 @@ __global__ void __launch_bounds__(kTotThreads) k_totals_partial(Tot5 p, size_t n
   double acc[5] = {0, 0, 0, 0, 0};
   for (size_t i = lo + threadIdx.x; i < hi; i += kTotThreads) {
 #pragma unroll
-    for (int k = 0; k < 5; ++k) acc[k] += double(static_cast<const T*>(p.f[k])[i]);
+    for (int k = 0; k < 5; ++k) acc[k] += double(fv<T>(p.f, k, i));
   }
 #pragma unroll
   for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] = acc[k];
@@ -220,38 +226,38 @@ __global__ void k_frozen_capture(Tot5 p, T* frozen, int nx, int ny, int nz, size
       n = nz;
     }
     size_t edge = base + (side == 0 ? 0 : (size_t)(n - 1) * stride);
-    frozen[g] = static_cast<const T*>(p.f[field])[edge];
+    frozen[g] = fv<T>(p.f, field, edge);
   }
 }
 
 }  // namespace
 
-cudaError_t launch_from_f64(const double* src, void* dst, size_t n, int is32, cudaStream_t s) {
+cudaError_t launch_from_f64(const double* src, void* dst, long long dstride, size_t n, int is32,
+                            cudaStream_t s) {
   if (!n) return cudaSuccess;
   if (is32)
-    k_from_f64<float><<<grid_for(n), kThreads, 0, s>>>(src, (float*)dst, n);
+    k_from_f64<float><<<grid_for(n), kThreads, 0, s>>>(src, (float*)dst, dstride, n);
   else
-    k_from_f64<double><<<grid_for(n), kThreads, 0, s>>>(src, (double*)dst, n);
+    k_from_f64<double><<<grid_for(n), kThreads, 0, s>>>(src, (double*)dst, dstride, n);
   return cudaGetLastError();
 }
 
-cudaError_t launch_to_f64(const void* src, double* dst, size_t n, int is32, cudaStream_t s) {
+cudaError_t launch_to_f64(const void* src, long long sstride, double* dst, size_t n, int is32,
+                          cudaStream_t s) {
   if (!n) return cudaSuccess;
   if (is32)
-    k_to_f64<float><<<grid_for(n), kThreads, 0, s>>>((const float*)src, dst, n);
+    k_to_f64<float><<<grid_for(n), kThreads, 0, s>>>((const float*)src, sstride, dst, n);
   else
-    k_to_f64<double><<<grid_for(n), kThreads, 0, s>>>((const double*)src, dst, n);
+    k_to_f64<double><<<grid_for(n), kThreads, 0, s>>>((const double*)src, sstride, dst, n);
   return cudaGetLastError();
 }
 
-cudaError_t launch_prim2cons(const double* const prim[5], void* const cons[5], size_t n, int is32,
-                             EosParams eos, cudaStream_t s) {
+cudaError_t launch_prim2cons(const double* const prim[5], const FieldView& cons, size_t n,
+                             int is32, EosParams eos, cudaStream_t s) {
   if (!n) return cudaSuccess;
   Ptr5 p;
-  for (int k = 0; k < 5; ++k) {
-    p.in[k] = prim[k];
-    p.out[k] = cons[k];
-  }
+  for (int k = 0; k < 5; ++k) p.in[k] = prim[k];
+  p.out = cons;
   if (is32)
     k_prim2cons<float><<<grid_for(n), kThreads, 0, s>>>(p, n, eos);
   else
@@ -259,11 +265,11 @@ cudaError_t launch_prim2cons(const double* const prim[5], void* const cons[5], s
   return cudaGetLastError();
 }
 
-cudaError_t launch_recover(const void* const cons[5], double* const prim[6], size_t n, int is32,
+cudaError_t launch_recover(const FieldView& cons, double* const prim[6], size_t n, int is32,
                            EosParams eos, cudaStream_t s) {
   if (!n) return cudaSuccess;
   Rec6 r;
-  for (int k = 0; k < 5; ++k) r.in[k] = cons[k];
+  r.in = cons;
   for (int k = 0; k < 6; ++k) r.out[k] = prim[k];
   if (is32)
     k_recover<float><<<grid_for(n), kThreads, 0, s>>>(r, n, eos);
@@ -297,10 +303,10 @@ int totals_blocks(size_t n) {
   return (int)b;
 }
 
-cudaError_t launch_totals(const void* const f[5], size_t n, int is32, double* partials,
-                          double* out, cudaStream_t s) {
+cudaError_t launch_totals(const FieldView& f, size_t n, int is32, double* partials, double* out,
+                          cudaStream_t s) {
   Tot5 p;
-  for (int k = 0; k < 5; ++k) p.f[k] = f[k];
+  p.f = f;
   int nb = totals_blocks(n);
   size_t chunk = (n + nb - 1) / nb;
   if (is32)
@@ -322,11 +328,11 @@ size_t frozen_axis_offset(int nx, int ny, int nz, int axis) {
 
 size_t frozen_elems(int nx, int ny, int nz) { return frozen_axis_offset(nx, ny, nz, 3); }
 
-cudaError_t launch_frozen_capture(const void* const f[5], void* frozen, int nx, int ny, int nz,
+cudaError_t launch_frozen_capture(const FieldView& f, void* frozen, int nx, int ny, int nz,
                                   int is32, cudaStream_t s) {
   size_t total = frozen_elems(nx, ny, nz);
   Tot5 p;
-  for (int k = 0; k < 5; ++k) p.f[k] = f[k];
+  p.f = f;
   if (is32)
     k_frozen_capture<float><<<grid_for(total), kThreads, 0, s>>>(p, (float*)frozen, nx, ny, nz,
                                                                  total);

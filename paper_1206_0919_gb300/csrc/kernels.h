@@ -14,6 +14,18 @@ namespace shasta {
 cudaError_t launch_sweep_f64(const SweepParams& P, int axis, int eos, cudaStream_t s);
 cudaError_t launch_sweep_f32(const SweepParams& P, int axis, int eos, cudaStream_t s);
 cudaError_t launch_sweep_mixed(const SweepParams& P, int axis, int eos, cudaStream_t s);
+// Resident warps per SM of the FP32 / mixed sweep kernels (launch variant).
+int sweep_warps_per_sm_f32(int axis, int variant);
+int sweep_warps_per_sm_mixed(int axis, int variant);
+
+// Where the five fields of a state live: element i of field k is at
+// p[k] + i * s[k] (in elements of the storage type).  FP64 states are five
+// dense arrays (s = 1); FP32 states keep (E, Mx, My, Mz) as one 16-byte quad
+// per cell (p[k] = quad + k, s = 4) and R as a dense array.
+struct FieldView {
+  void* p[5];
+  long long s[5];
+};
 
 // Physics constants handed to the auxiliary kernels.
 struct EosParams {
@@ -23,11 +35,13 @@ struct EosParams {
 };
 
 // Auxiliary kernels (aux.cu).  `is32` selects float (1) or double (0) storage.
-cudaError_t launch_from_f64(const double* src, void* dst, size_t n, int is32, cudaStream_t s);
-cudaError_t launch_to_f64(const void* src, double* dst, size_t n, int is32, cudaStream_t s);
-cudaError_t launch_prim2cons(const double* const prim[5], void* const cons[5], size_t n,
+cudaError_t launch_from_f64(const double* src, void* dst, long long dstride, size_t n, int is32,
+                            cudaStream_t s);
+cudaError_t launch_to_f64(const void* src, long long sstride, double* dst, size_t n, int is32,
+                          cudaStream_t s);
+cudaError_t launch_prim2cons(const double* const prim[5], const FieldView& cons, size_t n,
                              int is32, EosParams eos, cudaStream_t s);
-cudaError_t launch_recover(const void* const cons[5], double* const prim[6], size_t n, int is32,
+cudaError_t launch_recover(const FieldView& cons, double* const prim[6], size_t n, int is32,
                            EosParams eos, cudaStream_t s);
 // Counts cells with non-finite values, E < 0 or |M| >= E (cons) or e < 0,
 // n < 0, |v| >= 1 (prims) into *count (device).
@@ -38,12 +52,12 @@ cudaError_t launch_check_prims(const double* const f[5], size_t n, unsigned long
 // Totals: per-block partial sums into `partials` (5 * nblocks doubles, device
 // scratch), then one block sums them in fixed order into out[5] (device).
 int totals_blocks(size_t n);
-cudaError_t launch_totals(const void* const f[5], size_t n, int is32, double* partials,
-                          double* out, cudaStream_t s);
+cudaError_t launch_totals(const FieldView& f, size_t n, int is32, double* partials, double* out,
+                          cudaStream_t s);
 // Frozen ghost store: for each axis a block [side][layer][field][plane].
 size_t frozen_elems(int nx, int ny, int nz);
 size_t frozen_axis_offset(int nx, int ny, int nz, int axis);
-cudaError_t launch_frozen_capture(const void* const f[5], void* frozen, int nx, int ny, int nz,
+cudaError_t launch_frozen_capture(const FieldView& f, void* frozen, int nx, int ny, int nz,
                                   int is32, cudaStream_t s);
 
 }  // namespace shasta

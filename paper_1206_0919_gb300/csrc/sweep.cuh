@@ -61,8 +61,12 @@ struct SweepParams {
   unsigned long long* clamp_count;  // cells recovered with |M| clamped or E <= 0
   int seg_len;                      // fast kernels: cells per line segment (multiple of 8)
   int nseg;                         // fast kernels: segments per line
-  long long fstride;                // fast kernels: in[k] = in[0] + k*fstride (same for out)
   int variant;                      // fast kernels: launch variant (0: 3 CTAs/SM, 1: 2 CTAs/SM)
+  // fast kernels: state as (E, Mx, My, Mz) quads per cell plus an R array
+  const float* qin;
+  const float* rin;
+  float* qout;
+  float* rout;
 };
 
 // ------------------------------------------------------------- recovery ----

@@ -4,6 +4,9 @@
 // recovery at n+1/2, full step from the old state), reorganised for
 // throughput on Blackwell:
 //
+//  * State layout: (E, Mx, My, Mz) as one 16-byte quad per cell and R as a
+//    separate array.  A cell moves with one 16-byte and one 4-byte access,
+//    and the quad splits into the register pairs (E, Mx), (My, Mz).
 //  * One warp streams 32 lines (one per lane) along the sweep axis.  Lines
 //    may be cut into segments (each with its own 6-cell halo per side) so
 //    that small grids still fill the machine.
@@ -11,17 +14,17 @@
 //    with cp.async ahead of use.  For y/z sweeps each lane copies its own
 //    line (the lanes of one position are adjacent in memory).  For x sweeps
 //    the warp copies chunks of 8 positions x 32 rows cooperatively (8 lanes
-//    per 32-byte row segment) and writes results back the same way from the
-//    ring entries it no longer needs, so global accesses stay
+//    per 128-byte row segment of quads) and writes results back the same way
+//    from ring entries it no longer needs, so global accesses stay
 //    sector-complete.
-//  * The five fields travel as two packed pairs, (E, M_par) and
-//    (M_t1, M_t2), plus R: transport, differences and the antidiffusive
-//    flux use the packed f32x2 add/sub/mul/fma of sm_100+ (two fields per
-//    instruction); the flux limiter uses the three-input min.
-//  * The loop is unrolled by 4 and every register window is a circular
-//    buffer indexed at compile time: no window shifting.  Blocks of
-//    iterations that touch no ghost position run a variant without boundary
-//    logic.
+//  * Transport, differences and the antidiffusive flux run on the field
+//    pairs with the packed f32x2 add/sub/mul/fma of sm_100+; the flux
+//    limiter uses the three-input min.
+//  * The pass is written with differences (Delta, their first and second
+//    differences, Delta-hat) so that every carried quantity spans at most two
+//    positions: the loop is unrolled by 2 and all windows are renamed
+//    registers.  Old values are consumed before a same-parity slot is
+//    overwritten, so no copies are needed.
 //  * The old state for the full step is re-read from the ring (it is still
 //    resident) instead of being carried in registers.
 //  * Transport factors use Q-_j = 1 - Q+_{j-1}, exact for Eq. shasta-diff
@@ -29,7 +32,8 @@
 //    needs one division per pass.
 //  * The baryon density R is not transported at the half step: only E and M
 //    enter the recovery at n+1/2.
-//  * Recovery for p = e/3 uses D = E^2 - |M|^2:  s = sqrt(E^2 + 3D),
+//  * Recoveries at n (newest cell) and n+1/2 (four cells back) run together
+//    on packed pairs.  For p = e/3 with D = E^2 - |M|^2: s = sqrt(E^2 + 3D),
 //    p = D/(E + s), v = M/(E + p).  MIXED evaluates D in double-float
 //    (error-free products and sums on the FP32 pipe), which removes the
 //    cancellation as v -> 1 at about FP64 accuracy of D.
@@ -45,14 +49,16 @@ namespace fast {
 constexpr int LANES = 32;
 constexpr int CH = 8;      // x sweep: positions per cooperative chunk
 constexpr int XSLOTS = 3;  // x sweep: chunk slots (previous, current, next)
-// x ring slot: pair planes [row][pos][2] with row stride 18 (conflict-free
-// 64-bit reads down a column), R plane [row][pos] with row stride 9.
-constexpr int XPSTR = 2 * CH + 2;
+// x ring slot: quad plane [row][pos][4] with row stride 36 (16-byte units
+// 9 apart: conflict-free 128-bit accesses down a column), R plane [row][pos]
+// with row stride 9.
+constexpr int XQSTR = 4 * CH + 4;
 constexpr int XRSTR = CH + 1;
-constexpr int XPAIR = LANES * XPSTR;              // 576 floats
-constexpr int XSLOT = 2 * XPAIR + LANES * XRSTR;  // 1440 floats
-// y/z ring slot: pair rows [lane][2] (64 floats each), R row [lane]
-constexpr int YSLOT = 2 * 2 * LANES + LANES;      // 160 floats
+constexpr int XQ = LANES * XQSTR;         // 1152 floats
+constexpr int XSLOT = XQ + LANES * XRSTR; // 1440 floats
+// y/z ring slot: quad row [lane][4] (128 floats), R row [lane]
+constexpr int YQ = 4 * LANES;
+constexpr int YSLOT = YQ + LANES;         // 160 floats
 
 // ------------------------------------------------------- packed f32x2 ----
 
@@ -65,6 +71,16 @@ __device__ __forceinline__ f2 pk(float lo, float hi) {
 }
 __device__ __forceinline__ void up(f2 v, float& lo, float& hi) {
   asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ float lo_of(f2 v) {
+  float a, b;
+  up(v, a, b);
+  return a;
+}
+__device__ __forceinline__ float hi_of(f2 v) {
+  float a, b;
+  up(v, a, b);
+  return b;
 }
 __device__ __forceinline__ f2 add2(f2 a, f2 b) {
   f2 r;
@@ -91,8 +107,6 @@ __device__ __forceinline__ float min3f(float a, float b, float c) {
   asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
   return r;
 }
-// negates the high half (M_par of pair (E, M_par))
-__device__ __forceinline__ f2 neg_hi(f2 v) { return v ^ 0x8000000000000000ull; }
 
 // ---------------------------------------------------------- cp.async ----
 
@@ -101,6 +115,10 @@ __device__ __forceinline__ unsigned smem_u32(const void* p) {
 }
 __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src)
                : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
@@ -129,44 +147,41 @@ __device__ __forceinline__ bool flips(int q, int n, int bc) {
   return m >= n;
 }
 
-// Global field index of sweep-order field f (E, M_par, M_t1, M_t2, R).
+// Negates the momentum along the sweep in the pair that holds it:
+// x -> hi of (E, Mx); y -> lo of (My, Mz); z -> hi of (My, Mz).
 template <int AXIS>
-__device__ __forceinline__ int gfield(int f) {
-  constexpr int FPAR = 1 + AXIS;
-  constexpr int FT1 = AXIS == 0 ? 2 : 1;
-  constexpr int FT2 = AXIS == 2 ? 2 : 3;
-  return f == 0 ? 0 : (f == 1 ? FPAR : (f == 2 ? FT1 : (f == 3 ? FT2 : 4)));
+__device__ __forceinline__ void negate_par(f2& A, f2& B) {
+  if (AXIS == 0) A ^= 0x8000000000000000ull;
+  if (AXIS == 1) B ^= 0x0000000080000000ull;
+  if (AXIS == 2) B ^= 0x8000000000000000ull;
 }
 
-// Global address of sweep-order field f at extended position q of line t.
-template <int AXIS>
-__device__ __forceinline__ const float* src_addr(const SweepParams& P, int f, long long base,
-                                                 long long t, int q, int n) {
-  const int gf = gfield<AXIS>(f);
+// Copies extended position q of a line (first cell `cell0`, cell stride
+// `stride`) into a ring entry (quad at dq, R at dr).  Ghost positions follow
+// the boundary rule; frozen ghosts come from the frozen store (line t).
+__device__ __forceinline__ void copy_cell(const SweepParams& P, float* dq, float* dr,
+                                          long long cell0, long long stride, long long t, int q,
+                                          int n) {
   if (P.bc == BC_FROZEN && (q < 0 || q >= n)) {
     const int side = q < 0 ? 0 : 1;
     int layer = q < 0 ? -1 - q : q - n;
     layer = layer > NG - 1 ? NG - 1 : layer;
-    return static_cast<const float*>(P.frozen) + ((long long)(side * NG + layer) * NF + gf) * P.plane + t;
+    const float* fz = static_cast<const float*>(P.frozen) + (long long)(side * NG + layer) * NF * P.plane + t;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) cp_async4(dq + f, fz + f * P.plane);
+    cp_async4(dr, fz + 4 * P.plane);
+    return;
   }
-  return static_cast<const float*>(P.in[gf]) + base + (long long)map_pos(q, n, P.bc) * P.stride;
-}
-
-// Offset of sweep-order field f of a position inside a ring slot.
-template <bool XP>
-__device__ __forceinline__ int ring_off(int f, int row, int pos) {
-  if (XP) {
-    if (f < 4) return (f >> 1) * XPAIR + row * XPSTR + pos * 2 + (f & 1);
-    return 2 * XPAIR + row * XRSTR + pos;
-  }
-  if (f < 4) return (f >> 1) * (2 * LANES) + row * 2 + (f & 1);
-  return 4 * LANES + row;
+  const long long c = cell0 + (long long)map_pos(q, n, P.bc) * stride;
+  cp_async16(dq, P.qin + 4 * c);
+  cp_async4(dr, P.rin + c);
 }
 
 // ----------------------------------------------------------- recovery ----
 
 // Velocity along the sweep and pressure, FP32 (MIXED: D in double-float).
-// Returns 1 if |M| was clamped or E <= 0, else 0.
+// m1 is the momentum along the sweep.  Returns 1 if |M| was clamped or
+// E <= 0, else 0.
 template <int EOS, bool MIXED>
 __device__ __forceinline__ unsigned rec32(float E, float m1, float m2, float m3, float omd,
                                           float B, float ec, float& w, float& p) {
@@ -228,25 +243,26 @@ __device__ __forceinline__ unsigned rec32(float E, float m1, float m2, float m3,
   return clamped;
 }
 
-// Two independent recoveries at once (halves lo, hi), ideal gas, packed.
-// Clamped or vacuum cells fall back to the scalar routine.  Returns the
-// clamp flag of the lo half.
+// Two independent recoveries at once (halves lo, hi): E, the three momenta
+// and the momentum along the sweep, packed.  Clamped or vacuum cells, the
+// bag EoS and MIXED take the scalar routine.  Returns the lo clamp flag.
 template <int EOS, bool MIXED>
-__device__ __forceinline__ unsigned rec2(f2 E, f2 m1, f2 m2, f2 m3, f2 omd2, float omd, float B,
-                                         float ec, f2& w, f2& p) {
-  if (EOS == EOS_BAG || MIXED) {
+__device__ __forceinline__ unsigned rec2(f2 E, f2 mx, f2 my, f2 mz, f2 mpar, f2 mt1, f2 mt2,
+                                         f2 omd2, float omd, float B, float ec, f2& w, f2& p) {
+  auto scalar = [&]() -> unsigned {
     float El, Eh, al, ah, bl, bh, cl, ch, wl, wh_, pl, ph;
     up(E, El, Eh);
-    up(m1, al, ah);
-    up(m2, bl, bh);
-    up(m3, cl, ch);
+    up(mpar, al, ah);
+    up(mt1, bl, bh);
+    up(mt2, cl, ch);
     const unsigned c = rec32<EOS, MIXED>(El, al, bl, cl, omd, B, ec, wl, pl);
     rec32<EOS, MIXED>(Eh, ah, bh, ch, omd, B, ec, wh_, ph);
     w = pk(wl, wh_);
     p = pk(pl, ph);
     return c;
-  }
-  const f2 M2 = fma2(m1, m1, fma2(m2, m2, mul2(m3, m3)));
+  };
+  if (EOS == EOS_BAG || MIXED) return scalar();
+  const f2 M2 = fma2(mx, mx, fma2(my, my, mul2(mz, mz)));
   const f2 E2 = mul2(E, E);
   const f2 lim = mul2(omd2, E);
   const f2 L2 = mul2(lim, lim);
@@ -254,27 +270,16 @@ __device__ __forceinline__ unsigned rec2(f2 E, f2 m1, f2 m2, f2 m3, f2 omd2, flo
   up(M2, M2l, M2h);
   up(L2, L2l, L2h);
   up(E, El, Eh);
-  if (M2l > L2l || M2h > L2h || !(El > 0.0f) || !(Eh > 0.0f)) {
-    float al, ah, bl, bh, cl, ch, wl, wh_, pl, ph;
-    up(m1, al, ah);
-    up(m2, bl, bh);
-    up(m3, cl, ch);
-    const unsigned c = rec32<EOS, MIXED>(El, al, bl, cl, omd, B, ec, wl, pl);
-    rec32<EOS, MIXED>(Eh, ah, bh, ch, omd, B, ec, wh_, ph);
-    w = pk(wl, wh_);
-    p = pk(pl, ph);
-    return c;
-  }
+  if (M2l > L2l || M2h > L2h || !(El > 0.0f) || !(Eh > 0.0f)) return scalar();
   const f2 D = sub2(E2, M2);
   float tl, th;
   up(fma2(pk(3.0f, 3.0f), D, E2), tl, th);
-  const f2 den = add2(E, pk(sqrtf(tl), sqrtf(th)));
   float dl, dh;
-  up(den, dl, dh);
+  up(add2(E, pk(sqrtf(tl), sqrtf(th))), dl, dh);
   p = mul2(D, pk(__fdividef(1.0f, dl), __fdividef(1.0f, dh)));
   float hl, hh;
   up(add2(E, p), hl, hh);
-  w = mul2(m1, pk(__fdividef(1.0f, hl), __fdividef(1.0f, hh)));
+  w = mul2(mpar, pk(__fdividef(1.0f, hl), __fdividef(1.0f, hh)));
   return 0u;
 }
 
@@ -290,44 +295,6 @@ __device__ __forceinline__ float limit(float aph, float dhp, float dhm) {
   return __uint_as_float(__float_as_uint(mm) ^ sg);
 }
 
-// Limited phoenical antidiffusive flux through face j+1/2 for a field pair,
-// from the transported values at j-1..j+2 and the old differences
-// Delta_{j-1}, Delta_j, Delta_{j+1}.  The sign s = sgn(aph) (+1 for +0) is
-// applied by packed multiplies: A = s max(0, min(s dhp, s aph, s dhm)).
-__device__ __forceinline__ f2 afx2(f2 h0, f2 h1, f2 h2, f2 h3, f2 dm, f2 d, f2 dp, f2 eta2,
-                                   f2 m2, f2 m8) {
-  const f2 dhm = sub2(h1, h0);
-  const f2 dh = sub2(h2, h1);
-  const f2 dhp = sub2(h3, h2);
-  const f2 aph = mul2(eta2, fma2(m8, fma2(m2, d, add2(dp, dm)), dh));
-  const f2 sg = (aph & 0x8000000080000000ull) | 0x3f8000003f800000ull;  // +-1 per half
-  float p0, p1, a0, a1, q0, q1;
-  up(mul2(sg, dhp), p0, p1);
-  up(mul2(sg, aph), a0, a1);
-  up(mul2(sg, dhm), q0, q1);
-  return mul2(sg, pk(fmaxf(min3f(p0, a0, q0), 0.0f), fmaxf(min3f(p1, a1, q1), 0.0f)));
-}
-
-__device__ __forceinline__ float afx1(float h0, float h1, float h2, float h3, float dm, float d,
-                                      float dp, float eta) {
-  const float dhm = h1 - h0;
-  const float dh = h2 - h1;
-  const float dhp = h3 - h2;
-  const float aph = eta * fmaf(-0.125f, fmaf(-2.0f, d, dp + dm), dh);
-  return limit(aph, dhp, dhm);
-}
-
-// Shared memory per warp, in floats.
-template <int AXIS, int RING>
-struct Smem {
-  static constexpr int per_warp = AXIS == 0 ? XSLOTS * XSLOT : RING * YSLOT;
-};
-
-template <int V>
-using ic = std::integral_constant<int, V>;
-template <bool V>
-using bc_ = std::integral_constant<bool, V>;
-
 // ------------------------------------------------------ line pipeline ----
 //
 // One SHASTA pass of a field pair along the line, written with differences
@@ -338,79 +305,83 @@ using bc_ = std::integral_constant<bool, V>;
 //   DD_{k-1}    = Delta_{k-1} - Delta_{k-2},  D2_{k-2} = DD_{k-1} - DD_{k-2}
 //   Dh_{k-2}    = Uhat_{k-1} - Uhat_{k-2}                                   [Delta-hat]
 //   A_{k-3}     = limit(eta (Dh_{k-3} - D2_{k-3}/8), Dh_{k-2}, Dh_{k-4})    [phoenical + limiter]
-//   out_{k-3}   = Uhat_{k-3} - (A_{k-3} - A_{k-4})                          [Eq. shasta-n]
+//   out_{k-3}   = (Uhat_{k-3} + A_{k-4}) - A_{k-3}                          [Eq. shasta-n]
 // Two-slot arrays are indexed by position parity; K is the parity of k.
 struct Line2 {
-  f2 Up;     // U_{k-1}
-  f2 D[2];   // Delta by parity
+  f2 Up[2];  // U by parity
+  f2 D[2];   // Delta
   f2 DD[2];  // first difference of Delta
   f2 D2[2];  // second difference of Delta
   f2 Uh[2];  // transported values
   f2 Dh[2];  // their differences
-  f2 A;      // limited flux of the previous face
+  f2 A[2];   // limited fluxes
 };
 struct Line1 {
-  float Up, D[2], DD[2], D2[2], Uh[2], Dh[2], A;
+  float Up[2], D[2], DD[2], D2[2], Uh[2], Dh[2], A[2];
 };
 
 template <int K, bool SRC>
 __device__ __forceinline__ f2 step2(Line2& s, f2 u, f2 a2, f2 nb2, f2 c2, f2 src, f2 eta2, f2 m8) {
   constexpr int P0 = K & 1, P1 = (K + 1) & 1;  // parity of k (= k-2, k-4) and of k-1 (= k-3)
-  const f2 d = sub2(u, s.Up);                                    // Delta_{k-1}
-  f2 uh = fma2(c2, s.Up, fma2(a2, d, mul2(nb2, s.D[P0])));       // Uhat_{k-1}
+  // values whose slots are overwritten below are consumed first
+  const f2 aph = mul2(eta2, fma2(m8, s.D2[P1], s.Dh[P1]));        // A^ph_{k-3}
+  const f2 sg = (aph & 0x8000000080000000ull) | 0x3f8000003f800000ull;  // +-1
+  const f2 qm = mul2(sg, s.Dh[P0]);                              // s Dh_{k-4}
+  const f2 t = add2(s.Uh[P1], s.A[P0]);                          // Uhat_{k-3} + A_{k-4}
+  const f2 d = sub2(u, s.Up[P1]);                                // Delta_{k-1}
+  f2 uh = fma2(c2, s.Up[P1], fma2(a2, d, mul2(nb2, s.D[P0])));    // Uhat_{k-1}
   if (SRC) uh = add2(uh, src);
   const f2 dd = sub2(d, s.D[P0]);                                // DD_{k-1}
   const f2 d2 = sub2(dd, s.DD[P0]);                              // D2_{k-2}
   const f2 dh = sub2(uh, s.Uh[P0]);                              // Dh_{k-2}
-  const f2 aph = mul2(eta2, fma2(m8, s.D2[P1], s.Dh[P1]));        // A^ph_{k-3}
-  const f2 sg = (aph & 0x8000000080000000ull) | 0x3f8000003f800000ull;
   float p0, p1, a0, a1, q0, q1;
   up(mul2(sg, dh), p0, p1);
   up(mul2(sg, aph), a0, a1);
-  up(mul2(sg, s.Dh[P0]), q0, q1);
+  up(qm, q0, q1);
   const f2 A = mul2(sg, pk(fmaxf(min3f(p0, a0, q0), 0.0f), fmaxf(min3f(p1, a1, q1), 0.0f)));
-  const f2 out = sub2(s.Uh[P1], sub2(A, s.A));                   // out_{k-3}
-  s.A = A;
-  s.Up = u;
+  s.A[P1] = A;
+  s.Up[P0] = u;
   s.D[P1] = d;
   s.DD[P1] = dd;
   s.D2[P0] = d2;
   s.Uh[P1] = uh;
   s.Dh[P0] = dh;
-  return out;
+  return sub2(t, A);
 }
 
 template <int K>
 __device__ __forceinline__ float step1(Line1& s, float u, float a, float nb, float c, float eta) {
   constexpr int P0 = K & 1, P1 = (K + 1) & 1;
-  const float d = u - s.Up;
-  const float uh = fmaf(c, s.Up, fmaf(a, d, nb * s.D[P0]));
+  const float aph = eta * fmaf(-0.125f, s.D2[P1], s.Dh[P1]);
+  const float qm = s.Dh[P0];
+  const float t = s.Uh[P1] + s.A[P0];
+  const float d = u - s.Up[P1];
+  const float uh = fmaf(c, s.Up[P1], fmaf(a, d, nb * s.D[P0]));
   const float dd = d - s.D[P0];
   const float d2 = dd - s.DD[P0];
   const float dh = uh - s.Uh[P0];
-  const float A = limit(eta * fmaf(-0.125f, s.D2[P1], s.Dh[P1]), dh, s.Dh[P0]);
-  const float out = s.Uh[P1] - (A - s.A);
-  s.A = A;
-  s.Up = u;
+  const float A = limit(aph, dh, qm);
+  s.A[P1] = A;
+  s.Up[P0] = u;
   s.D[P1] = d;
   s.DD[P1] = dd;
   s.D2[P0] = d2;
   s.Uh[P1] = uh;
   s.Dh[P0] = dh;
-  return out;
+  return t - A;
 }
 
 __device__ __forceinline__ void init2(Line2& s, f2 u0) {
   const f2 z = pk(0.0f, 0.0f);
-  s.Up = u0;
-  s.A = z;
 #pragma unroll
-  for (int k = 0; k < 2; ++k) s.D[k] = s.DD[k] = s.D2[k] = s.Uh[k] = s.Dh[k] = z;
+  for (int k = 0; k < 2; ++k) {
+    s.Up[k] = u0;
+    s.A[k] = s.D[k] = s.DD[k] = s.D2[k] = s.Uh[k] = s.Dh[k] = z;
+  }
 }
 __device__ __forceinline__ void init1(Line1& s) {
-  s.Up = s.A = 0.0f;
 #pragma unroll
-  for (int k = 0; k < 2; ++k) s.D[k] = s.DD[k] = s.D2[k] = s.Uh[k] = s.Dh[k] = 0.0f;
+  for (int k = 0; k < 2; ++k) s.Up[k] = s.A[k] = s.D[k] = s.DD[k] = s.D2[k] = s.Uh[k] = s.Dh[k] = 0.0f;
 }
 
 // Transport coefficients of cell k-1 from w_{k-1}, w_k and Q+_{k-2}:
@@ -425,6 +396,33 @@ __device__ __forceinline__ void coeffs(float tau, float w1, float w0, float& qpr
   nb = -0.5f * qm * qm;
   c = qp + qm;
 }
+
+// Pressure sources of the pairs (E, Mx) and (My, Mz) from the difference of
+// (p w, p) two cells apart: E gets the p w term, the momentum along the
+// sweep the p term.
+template <int AXIS>
+__device__ __forceinline__ void sources(f2 ht2, float ht, f2 fdiff, f2& sA, f2& sB) {
+  if (AXIS == 0) {
+    sA = mul2(ht2, fdiff);
+    sB = pk(0.0f, 0.0f);
+  } else {
+    float pwd, pd;
+    up(fdiff, pwd, pd);
+    sA = pk(ht * pwd, 0.0f);
+    sB = AXIS == 1 ? pk(ht * pd, 0.0f) : pk(0.0f, ht * pd);
+  }
+}
+
+// Shared memory per warp, in floats.
+template <int AXIS, int RING>
+struct Smem {
+  static constexpr int per_warp = AXIS == 0 ? XSLOTS * XSLOT : RING * YSLOT;
+};
+
+template <int V>
+using ic = std::integral_constant<int, V>;
+template <bool V>
+using bc_ = std::integral_constant<bool, V>;
 
 // ------------------------------------------------------------- kernel ----
 //
@@ -442,20 +440,28 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParam
 
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const long long gw = (long long)blockIdx.x * WARPS + warp;
-  const long long ngroups = (P.plane + LANES - 1) / LANES;
-  const long long g = gw % ngroups;
-  const int seg = (int)(gw / ngroups);
-  if (seg >= P.nseg) return;  // whole warp
   float* wsm = smem + (size_t)warp * Smem<AXIS, RING>::per_warp;
-
   const int n = P.n;
+  const long long ngroups = (P.plane + LANES - 1) / LANES;
+  const long long nitems = ngroups * P.nseg;
+  const long long nwarps = (long long)gridDim.x * WARPS;
+  unsigned nclamp = 0;
+  // work items (line group g, segment seg), taken in a grid stride
+#pragma unroll 1
+  for (long long item = (long long)blockIdx.x * WARPS + warp; item < nitems; item += nwarps) {
+  const long long g = item % ngroups;
+  const int seg = (int)(item / ngroups);
   const long long t = g * LANES + lane;
   const bool valid = t < P.plane;
   const long long tl = valid ? t : P.plane - 1;
-  const long long base = (tl % P.nb) * P.sb + (tl / P.nb) * P.sc;
-  const int s0 = seg * P.seg_len;
-  const int s1 = min(s0 + P.seg_len, n);
+  const long long base = (tl % P.nb) * P.sb + (tl / P.nb) * P.sc;  // first cell of the line
+  // segments split the line evenly (x path: on 8-cell chunk boundaries)
+  int s0 = (int)(((long long)seg * n) / P.nseg);
+  int s1 = (int)(((long long)(seg + 1) * n) / P.nseg);
+  if (XP) {
+    s0 &= ~(CH - 1);
+    s1 = seg + 1 == P.nseg ? n : (s1 & ~(CH - 1));
+  }
   // positions streamed: qs .. qe (the x path starts on a chunk boundary)
   const int qs = XP ? ((s0 - 2 * NG) & ~(CH - 1)) : s0 - 2 * NG;
   const int qe = s1 + LAG - 1;
@@ -469,18 +475,14 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParam
   i2 = i2 < trip ? i2 : trip;
   if (i2 < i1) i2 = i1;
 
-  const float* in0 = static_cast<const float*>(P.in[0]);
-  float* out0 = static_cast<float*>(P.out[0]);
-  const long long fs = P.fstride;
   const float tau_h = float(P.tau_h), tau_f = float(P.tau_f);
   const float eta = float(P.eta);
   const float omd = float(P.omd), B = float(P.bag_B), ec = float(P.bag_ec);
+  const float htau_h = float(P.htau_h), htau_f = float(P.htau_f);
   const f2 omd2 = pk(omd, omd);
   const f2 eta2 = pk(eta, eta), m8c = pk(-0.125f, -0.125f);
-  const f2 ht_h = pk(float(P.htau_h), float(P.htau_h));
-  const f2 ht_f = pk(float(P.htau_f), float(P.htau_f));
+  const f2 ht_h2 = pk(htau_h, htau_h), ht_f2 = pk(htau_f, htau_f);
   const bool frozen = P.bc == BC_FROZEN;
-  unsigned nclamp = 0;
 
   auto x_slot = [&](int C) -> float* { return wsm + ((C + 3 * 4) % XSLOTS) * XSLOT; };
   // x path: cooperative copy of chunk C = positions [8C, 8C+8) of 32 rows
@@ -493,33 +495,38 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParam
       const int row = r0 + 4 * k;
       long long tr = g * LANES + row;
       tr = tr < P.plane ? tr : P.plane - 1;
+      float* dq = ring + row * XQSTR + pc * 4;
+      float* dr = ring + XQ + row * XRSTR + pc;
       if (ghost) {
-#pragma unroll
-        for (int f = 0; f < NF; ++f)
-          cp_async4(ring + ring_off<true>(f, row, pc), src_addr<AXIS>(P, f, tr * P.sb, tr, pos, n));
+        copy_cell(P, dq, dr, tr * P.sb, 1, tr, pos, n);
       } else {
-        const float* rp = in0 + tr * P.sb + pos;
-#pragma unroll
-        for (int f = 0; f < NF; ++f) cp_async4(ring + ring_off<true>(f, row, pc), rp + gfield<AXIS>(f) * fs);
+        const long long c = tr * P.sb + pos;
+        cp_async16(dq, P.qin + 4 * c);
+        cp_async4(dr, P.rin + c);
       }
     }
   };
   // y/z path: own-lane copy of position q into ring slot `slot`
   auto yz_issue = [&](float* slot, int q, bool ghost) {
+    float* dq = slot + lane * 4;
+    float* dr = slot + YQ + lane;
     if (ghost) {
-#pragma unroll
-      for (int f = 0; f < NF; ++f)
-        cp_async4(slot + ring_off<false>(f, lane, 0), src_addr<AXIS>(P, f, base, tl, q, n));
+      copy_cell(P, dq, dr, base, P.stride, tl, q, n);
     } else {
-      const float* rp = in0 + base + (long long)q * P.stride;
-#pragma unroll
-      for (int f = 0; f < NF; ++f) cp_async4(slot + ring_off<false>(f, lane, 0), rp + gfield<AXIS>(f) * fs);
+      const long long c = base + (long long)q * P.stride;
+      cp_async16(dq, P.qin + 4 * c);
+      cp_async4(dr, P.rin + c);
     }
   };
-  auto rd2 = [&](const float* slot, int pos, int p) -> f2 {
-    return *reinterpret_cast<const f2*>(slot + ring_off<XP>(2 * p, lane, pos));
+  // quad (as the pairs (E, Mx), (My, Mz)) and R of a ring entry
+  auto rdq = [&](const float* slot, int pos, f2& A, f2& Bp) {
+    const float4 v = *reinterpret_cast<const float4*>(XP ? slot + lane * XQSTR + pos * 4 : slot + lane * 4);
+    A = pk(v.x, v.y);
+    Bp = pk(v.z, v.w);
   };
-  auto rdR = [&](const float* slot, int pos) -> float { return slot[ring_off<XP>(4, lane, pos)]; };
+  auto rdr = [&](const float* slot, int pos) -> float {
+    return XP ? slot[XQ + lane * XRSTR + pos] : slot[YQ + lane];
+  };
 
   // prologue
   if (XP) {
@@ -533,7 +540,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParam
     }
   }
 
-  // per-line state: pairs A = (E, M_par), B = (M_t1, M_t2)
+  // per-line state: pairs A = (E, Mx), B = (My, Mz)
   Line2 hA, hB, fA, fB;  // half-step and full-step passes
   Line1 fR;              // full-step pass of R
   init2(hA, pk(1.0f, 0.0f));
@@ -548,9 +555,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParam
   float qph = 0.5f, qpf = 0.5f;                 // Q+ of the previous cell
 
   // One streaming step at position q = qs + i + K (K = parity of q - qs).
-  //   sq, sq4: ring slots of positions q and q-4; pq, pq4: their chunk
-  //   offsets (x path); sjo: slot of output position q-7 (x path); siss:
-  //   slot receiving position q + DIST (y/z path).
+  //   sq, sq4: ring slots of positions q and q-4; sjo: slot of output
+  //   position q-7 (x path); siss: slot receiving position q + DIST (y/z).
   auto body = [&](int i, auto Kc, auto Gc, const float* sq, const float* sq4, float* sjo,
                   float* siss) {
     constexpr int K = decltype(Kc)::value;
@@ -561,9 +567,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParam
     const int pq4 = XP ? ((q - 4) & 7) : 0;
     if (!XP) cp_wait<DIST - 1>();
     // ---- U^n_q (E, M)
-    f2 uA = rd2(sq, pq, 0);
-    const f2 uB = rd2(sq, pq, 1);
-    if (GH && flips(q, n, P.bc)) uA = neg_hi(uA);
+    f2 uA, uB;
+    rdq(sq, pq, uA, uB);
+    if (GH && flips(q, n, P.bc)) negate_par<AXIS>(uA, uB);
     if (!XP) {
       if (GH) {
         if (q + DIST <= qe) yz_issue(siss, q + DIST, true);
@@ -576,14 +582,15 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParam
     float wn0, wh0;
     f2 fn0, fh0;
     {
-      float E0, m10, m20, m30, E1, m11, m21, m31;
-      up(uA, E0, m10);
-      up(uB, m20, m30);
-      up(HA, E1, m11);
-      up(HB, m21, m31);
+      const f2 E = pk(lo_of(uA), lo_of(HA));
+      const f2 mx = pk(hi_of(uA), hi_of(HA));
+      const f2 my = pk(lo_of(uB), lo_of(HB));
+      const f2 mz = pk(hi_of(uB), hi_of(HB));
+      const f2 mpar = AXIS == 0 ? mx : (AXIS == 1 ? my : mz);
+      const f2 mt1 = AXIS == 0 ? my : mx;
+      const f2 mt2 = AXIS == 2 ? my : mz;
       f2 w2, p2;
-      const unsigned c0 = rec2<EOS, MIXED>(pk(E0, E1), pk(m10, m11), pk(m20, m21), pk(m30, m31),
-                                           omd2, omd, B, ec, w2, p2);
+      const unsigned c0 = rec2<EOS, MIXED>(E, mx, my, mz, mpar, mt1, mt2, omd2, omd, B, ec, w2, p2);
       nclamp += ((unsigned)(q - s0) < (unsigned)(s1 - s0)) ? c0 : 0u;
       float pl, phi, pwl, pwh;
       up(w2, wn0, wh0);
@@ -596,36 +603,36 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParam
     {
       float a, nb, c;
       coeffs(tau_h, wn1, wn0, qph, a, nb, c);
-      const f2 src = mul2(ht_h, sub2(fn[P0], fn0));  // f_{q-2} - f_q
+      f2 sA, sB;
+      sources<AXIS>(ht_h2, htau_h, sub2(fn[P0], fn0), sA, sB);  // f_{q-2} - f_q
       fn[P0] = fn0;
       wn1 = wn0;
       const f2 a2 = pk(a, a), nb2 = pk(nb, nb), c2 = pk(c, c);
-      HA = step2<K, true>(hA, uA, a2, nb2, c2, src, eta2, m8c);
-      HB = step2<K, false>(hB, uB, a2, nb2, c2, src, eta2, m8c);
+      HA = step2<K, true>(hA, uA, a2, nb2, c2, sA, eta2, m8c);
+      HB = step2<K, AXIS != 0>(hB, uB, a2, nb2, c2, sB, eta2, m8c);
       if (GH && frozen && (q - NG < 0 || q - NG >= n)) {
         // frozen ghost: the half-step state is the stored ghost value
         const float* s3 = XP ? x_slot((q - NG) >> 3) : wsm + ((q - NG - qs) & (RING - 1)) * YSLOT;
-        const int p3 = XP ? ((q - NG) & 7) : 0;
-        HA = rd2(s3, p3, 0);
-        HB = rd2(s3, p3, 1);
+        rdq(s3, XP ? ((q - NG) & 7) : 0, HA, HB);
       }
     }
     // ---- full-step pass, newest cell q-4 (old state re-read): U^{n+1}_{q-7}
     f2 oA, oB;
     float oR;
     {
-      f2 vA = rd2(sq4, pq4, 0);
-      const f2 vB = rd2(sq4, pq4, 1);
-      const float vR = rdR(sq4, pq4);
-      if (GH && flips(q - 4, n, P.bc)) vA = neg_hi(vA);
+      f2 vA, vB;
+      rdq(sq4, pq4, vA, vB);
+      const float vR = rdr(sq4, pq4);
+      if (GH && flips(q - 4, n, P.bc)) negate_par<AXIS>(vA, vB);
       float a, nb, c;
       coeffs(tau_f, wh1, wh0, qpf, a, nb, c);
-      const f2 src = mul2(ht_f, sub2(fh[P0], fh0));  // f_{q-6} - f_{q-4}
+      f2 sA, sB;
+      sources<AXIS>(ht_f2, htau_f, sub2(fh[P0], fh0), sA, sB);  // f_{q-6} - f_{q-4}
       fh[P0] = fh0;
       wh1 = wh0;
       const f2 a2 = pk(a, a), nb2 = pk(nb, nb), c2 = pk(c, c);
-      oA = step2<K, true>(fA, vA, a2, nb2, c2, src, eta2, m8c);
-      oB = step2<K, false>(fB, vB, a2, nb2, c2, src, eta2, m8c);
+      oA = step2<K, true>(fA, vA, a2, nb2, c2, sA, eta2, m8c);
+      oB = step2<K, AXIS != 0>(fB, vB, a2, nb2, c2, sB, eta2, m8c);
       oR = step1<K>(fR, vR, a, nb, c, eta);
     }
     const int jo = q - LAG;
@@ -633,20 +640,19 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParam
       // the ring entry of position jo is dead: stage the result there
       if (jo >= s0 && jo < s1) {
         const int pj = jo & 7;
-        *reinterpret_cast<f2*>(sjo + ring_off<true>(0, lane, pj)) = oA;
-        *reinterpret_cast<f2*>(sjo + ring_off<true>(2, lane, pj)) = oB;
-        sjo[ring_off<true>(4, lane, pj)] = oR;
+        float o0, o1, o2, o3;
+        up(oA, o0, o1);
+        up(oB, o2, o3);
+        *reinterpret_cast<float4*>(sjo + lane * XQSTR + pj * 4) = make_float4(o0, o1, o2, o3);
+        sjo[XQ + lane * XRSTR + pj] = oR;
       }
     } else if (valid && jo >= s0 && jo < s1) {
-      float* op = out0 + base + (long long)jo * P.stride;
+      const long long c = base + (long long)jo * P.stride;
       float o0, o1, o2, o3;
       up(oA, o0, o1);
       up(oB, o2, o3);
-      op[gfield<AXIS>(0) * fs] = o0;
-      op[gfield<AXIS>(1) * fs] = o1;
-      op[gfield<AXIS>(2) * fs] = o2;
-      op[gfield<AXIS>(3) * fs] = o3;
-      op[gfield<AXIS>(4) * fs] = oR;
+      *reinterpret_cast<float4*>(P.qout + 4 * c) = make_float4(o0, o1, o2, o3);
+      P.rout[c] = oR;
     }
   };
 
@@ -705,9 +711,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParam
             const int row = r0 + 4 * k;
             const long long tr = g * LANES + row;
             if (tr < P.plane) {
-              float* op = out0 + tr * P.sb + pos;
-#pragma unroll
-              for (int f = 0; f < NF; ++f) op[gfield<AXIS>(f) * fs] = ring[ring_off<true>(f, row, pc)];
+              const long long c = tr * P.sb + pos;
+              *reinterpret_cast<float4*>(P.qout + 4 * c) =
+                  *reinterpret_cast<const float4*>(ring + row * XQSTR + pc * 4);
+              P.rout[c] = ring[XQ + row * XRSTR + pc];
             }
           }
         }
@@ -717,6 +724,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParam
     }
   }
   cp_wait<0>();
+  __syncwarp();
+  }  // work items
   if (nclamp && P.clamp_count) atomicAdd(P.clamp_count, (unsigned long long)nclamp);
 }
 
