@@ -85,12 +85,17 @@ typedef struct shasta_opts {
   int device;    /* CUDA device ordinal */
   int check_input; /* nonzero: set calls scan the state and return
                       SHASTA_EUNPHYSICAL for non-finite values, E < 0 or |M| >= E */
+  int autotune;    /* nonzero: the first shasta_step times launch choices (line
+                      segments, register variant) per axis and keeps the fastest;
+                      results do not depend on the choice */
+  int use_graphs;  /* nonzero: runs of six steps starting at phase 0 replay one
+                      captured CUDA graph of 18 sweeps */
 } shasta_opts;
 
 typedef struct shasta_ctx shasta_ctx;
 
 /* Fills *o with the defaults: FP32, eta = 1/8, delta = 0, stream NULL,
- * device 0, check_input 1. */
+ * device 0, check_input 1, autotune 1, use_graphs 1. */
 void shasta_default_opts(shasta_opts* o);
 
 /* Creates a solver for one event.  dx is the cell size, lambda = dt/dx the
@@ -135,6 +140,16 @@ shasta_status shasta_step(shasta_ctx* ctx, int nsteps);
  * shasta_step for a single axis.  Does not change the step counter; used to
  * time or study one sweep.  Errors: EINVAL (bad axis, state never set), ECUDA. */
 shasta_status shasta_sweep(shasta_ctx* ctx, int axis);
+
+/* Times the launch choices of the FP32 / MIXED sweep kernels for this grid
+ * (segments per line, register variant) and keeps the fastest per axis.
+ * Runs sweeps from the current state into the spare buffer only, so the
+ * state is unchanged; synchronous.  Errors: EINVAL (state not set), ECUDA. */
+shasta_status shasta_autotune(shasta_ctx* ctx);
+
+/* Current launch choice per axis: out[2a] = register variant, out[2a+1] =
+ * segments per line (FP64: unused). */
+shasta_status shasta_get_tuning(const shasta_ctx* ctx, int out[6]);
 
 /* Waits until all work enqueued on the context's stream has finished. */
 shasta_status shasta_sync(shasta_ctx* ctx);

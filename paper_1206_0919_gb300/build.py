@@ -3,8 +3,10 @@
 Translation units are compiled in parallel.  The FP64 units (the fused FP64
 sweep and the auxiliary maps) are built with ``-fmad=false`` and IEEE
 division / square root so that they evaluate each expression in plain double
-precision in source order; the FP32 / mixed sweeps use FMA contraction,
-flush-to-zero and fast division / square root.
+precision in source order; the FP32 / mixed sweeps use flush-to-zero and
+fast division / square root; their fused multiply-adds
+are explicit (also built with ``-fmad=false``, so that every instantiation of
+the streaming step rounds alike).
 """
 from __future__ import annotations
 
@@ -24,7 +26,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
           "--expt-relaxed-constexpr", "-I", CSRC, "-I", INCLUDE]
 EXACT = ["-fmad=false", "-prec-div=true", "-prec-sqrt=true", "-ftz=false"]
-FAST = ["-fmad=true", "-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
+FAST = ["-fmad=false", "-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
 
 UNITS = [
     ("api.cu", EXACT),

@@ -49,9 +49,14 @@ struct shasta_ctx {
   bool own_stream = false;
   int64_t steps = 0;
   int sm_count = 152;
-  int warps_per_sm = 12;  // segment target of the FP32 kernels
-  int force_nseg = 0;     // nonzero: segments per line (tuning)
-  int variant = 0;        // launch variant of the FP32 kernels (tuning)
+  int occ[2][3][2] = {};  // FP32 / MIXED: resident warps per SM [eos][axis][variant]
+  int wpb = 4;            // warps per block of the FP32 / MIXED kernels
+  int force_nseg = 0;     // nonzero: segments per line (environment override)
+  int force_variant = -1; // >= 0: launch variant (environment override)
+  bool tuned = false;     // autotuned launch choice below is valid
+  int tune_var[3] = {0, 0, 0};
+  int tune_nseg[3] = {1, 1, 1};
+  cudaGraphExec_t graph = nullptr;  // six steps from phase 0, buffer 0
   std::string err;
 };
 
@@ -153,7 +158,26 @@ shasta_status after_set(shasta_ctx* c) {
   return SHASTA_OK;
 }
 
-SweepParams sweep_params(shasta_ctx* c, int axis, int from) {
+// Segment count minimising ceil(items / resident warps) * (length + 13):
+// each segment re-reads a 6-cell halo per side and pays a 7-cell lag.
+int model_nseg(const shasta_ctx* c, int n, long long plane, int wpsm) {
+  const long long groups = (plane + 31) / 32;
+  const long long slots = (long long)c->sm_count * (wpsm > 0 ? wpsm : 1);
+  double best = 1e300;
+  int nseg = 1;
+  const int max_seg = n / 16 > 1 ? n / 16 : 1;
+  for (int k = 1; k <= max_seg && k <= 16; ++k) {
+    const long long waves = (groups * k + slots - 1) / slots;
+    const double cost = (double)waves * ((double)n / k + 13.0);
+    if (cost < best * 0.999) {
+      best = cost;
+      nseg = k;
+    }
+  }
+  return nseg;
+}
+
+SweepParams sweep_params(shasta_ctx* c, int axis, int from, int variant, int nseg) {
   SweepParams P;
   memset(&P, 0, sizeof P);
   long long nx = c->g.nx, ny = c->g.ny, nz = c->g.nz;
@@ -200,47 +224,100 @@ SweepParams sweep_params(shasta_ctx* c, int axis, int from) {
   P.bag_B = c->eos.B;
   P.bag_ec = c->eos.e_c;
   P.clamp_count = c->d_count;
-  // Lines are cut into segments (each re-reads a 6-cell halo per side and
-  // pays a 7-cell pipeline lag).  One wave of resident warps loops over the
-  // (line group, segment) items; the segment count minimises
-  // ceil(items / resident warps) * (segment length + 13).
-  int nseg = 1;
+  P.nseg = nseg < 1 ? 1 : nseg;
+  P.seg_len = (P.n + P.nseg - 1) / P.nseg;
+  P.variant = variant;
   if (c->o.precision != SHASTA_FP64) {
-    const long long groups = (P.plane + 31) / 32;
-    int wpsm = c->o.precision == SHASTA_MIXED ? sweep_warps_per_sm_mixed(axis, c->variant)
-                                              : sweep_warps_per_sm_f32(axis, c->variant);
-    if (wpsm < 1) wpsm = 1;
-    const long long slots = (long long)c->sm_count * wpsm;
-    double best = 1e300;
-    const int max_seg = P.n / 16 > 1 ? P.n / 16 : 1;
-    for (int k = 1; k <= max_seg && k <= 16; ++k) {
-      const long long items = groups * k;
-      const long long waves = (items + slots - 1) / slots;
-      const double cost = (double)waves * ((double)P.n / k + 13.0);
-      if (cost < best * 0.999) {
-        best = cost;
-        nseg = k;
-      }
-    }
-    if (c->force_nseg > 0) nseg = c->force_nseg;
+    // one wave of resident warps loops over the (line group, segment) items
+    const long long items = ((P.plane + 31) / 32) * P.nseg;
+    long long blocks = (items + c->wpb - 1) / c->wpb;
+    const int wpsm = c->occ[c->eos.kind][axis][variant];
+    const long long wave = (long long)c->sm_count * (wpsm > 0 ? wpsm / c->wpb : 1);
+    P.blocks = blocks < wave ? blocks : (wave > 0 ? wave : 1);
   }
-  P.seg_len = (P.n + nseg - 1) / nseg;
-  P.nseg = nseg;
-  P.variant = c->variant;
   return P;
 }
 
+// Launch choice of the FP32 / MIXED kernels for an axis: environment
+// overrides, else the autotuned choice, else variant 0 and the model.
+void launch_choice(const shasta_ctx* c, int axis, int& variant, int& nseg) {
+  variant = c->tuned ? c->tune_var[axis] : 0;
+  if (c->force_variant >= 0) variant = c->force_variant;
+  const int n = axis == 0 ? c->g.nx : (axis == 1 ? c->g.ny : c->g.nz);
+  const long long plane = axis == 0 ? (long long)c->g.ny * c->g.nz
+                                    : (axis == 1 ? (long long)c->g.nx * c->g.nz
+                                                 : (long long)c->g.nx * c->g.ny);
+  nseg = c->tuned ? c->tune_nseg[axis] : model_nseg(c, n, plane, c->occ[c->eos.kind][axis][variant]);
+  if (c->force_nseg > 0) nseg = c->force_nseg;
+}
+
+cudaError_t launch_params(shasta_ctx* c, int axis, const SweepParams& P) {
+  if (c->o.precision == SHASTA_FP64) return launch_sweep_f64(P, axis, c->eos.kind, c->stream);
+  if (c->o.precision == SHASTA_MIXED) return launch_sweep_mixed(P, axis, c->eos.kind, c->stream);
+  return launch_sweep_f32(P, axis, c->eos.kind, c->stream);
+}
+
 cudaError_t launch_sweep(shasta_ctx* c, int axis) {
-  SweepParams P = sweep_params(c, axis, c->cur);
-  cudaError_t e;
-  if (c->o.precision == SHASTA_FP64)
-    e = launch_sweep_f64(P, axis, c->eos.kind, c->stream);
-  else if (c->o.precision == SHASTA_MIXED)
-    e = launch_sweep_mixed(P, axis, c->eos.kind, c->stream);
-  else
-    e = launch_sweep_f32(P, axis, c->eos.kind, c->stream);
+  int variant, nseg;
+  launch_choice(c, axis, variant, nseg);
+  cudaError_t e = launch_params(c, axis, sweep_params(c, axis, c->cur, variant, nseg));
   if (e == cudaSuccess) c->cur ^= 1;
   return e;
+}
+
+void drop_graph(shasta_ctx* c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
+}
+
+// Times candidate launch choices per axis with repeated sweeps from the
+// current buffer into the other one (the state itself is not changed) and
+// keeps the fastest.  Segmenting and the variant do not change results.
+shasta_status autotune(shasta_ctx* c) {
+  if (c->o.precision == SHASTA_FP64) {
+    c->tuned = true;
+    return SHASTA_OK;
+  }
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0), "cudaEventCreate");
+  CK(cudaEventCreate(&e1), "cudaEventCreate");
+  shasta_status st = SHASTA_OK;
+  for (int axis = 0; axis < 3 && st == SHASTA_OK; ++axis) {
+    const int n = axis == 0 ? c->g.nx : (axis == 1 ? c->g.ny : c->g.nz);
+    float best = 1e30f;
+    int bv = 0, bn = 1;
+    const int max_seg = n / 16 > 1 ? n / 16 : 1;
+    for (int var = 0; var < 2; ++var)
+      for (int ns = 1; ns <= max_seg && ns <= 8; ++ns) {
+        SweepParams P = sweep_params(c, axis, c->cur, var, ns);
+        cudaError_t ce = cudaSuccess;
+        for (int r = 0; r < 2 && ce == cudaSuccess; ++r) ce = launch_params(c, axis, P);
+        if (ce == cudaSuccess) ce = cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < 4 && ce == cudaSuccess; ++r) ce = launch_params(c, axis, P);
+        if (ce == cudaSuccess) ce = cudaEventRecord(e1, c->stream);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+        if (ce != cudaSuccess) {
+          st = cuda_fail(c, ce, "autotune");
+          break;
+        }
+        if (ms < best) {
+          best = ms;
+          bv = var;
+          bn = ns;
+        }
+      }
+    c->tune_var[axis] = bv;
+    c->tune_nseg[axis] = bn;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st == SHASTA_OK) {
+    c->tuned = true;
+    drop_graph(c);
+  }
+  return st;
 }
 
 void release(shasta_ctx* c) {
@@ -253,6 +330,7 @@ void release(shasta_ctx* c) {
   cudaFree(c->d_tot);
   cudaFree(c->d_count);
   cudaFreeHost(c->h_small);
+  drop_graph(c);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -270,6 +348,8 @@ void shasta_default_opts(shasta_opts* o) {
   o->stream = nullptr;
   o->device = 0;
   o->check_input = 1;
+  o->autotune = 1;
+  o->use_graphs = 1;
 }
 
 shasta_status shasta_create(const shasta_grid* g, double dx, double lambda, const shasta_eos* eos,
@@ -331,12 +411,10 @@ shasta_status shasta_create(const shasta_grid* g, double dx, double lambda, cons
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) == cudaSuccess && sms > 0)
       c->sm_count = sms;
-    const char* v = getenv("SHASTA_WARPS_PER_SM");
-    if (v && atoi(v) > 0) c->warps_per_sm = atoi(v);
-    v = getenv("SHASTA_NSEG");
+    const char* v = getenv("SHASTA_NSEG");
     if (v && atoi(v) > 0) c->force_nseg = atoi(v);
     v = getenv("SHASTA_VARIANT");
-    if (v) c->variant = atoi(v);
+    if (v && atoi(v) >= 0 && atoi(v) <= 1) c->force_variant = atoi(v);
   }
   auto bail = [&](cudaError_t err, const char* where) {
     std::string m = std::string(where) + ": " + cudaGetErrorString(err);
@@ -381,6 +459,11 @@ shasta_status shasta_create(const shasta_grid* g, double dx, double lambda, cons
   if (err != cudaSuccess) return bail(err, "cudaMemset counters");
   err = cudaMallocHost((void**)&c->h_small, 16 * sizeof(double));
   if (err != cudaSuccess) return bail(err, "cudaMallocHost");
+  if (opts.precision != SHASTA_FP64) {
+    err = opts.precision == SHASTA_MIXED ? prepare_sweep_mixed(c->occ) : prepare_sweep_f32(c->occ);
+    if (err != cudaSuccess) return bail(err, "prepare sweep kernels");
+    c->wpb = opts.precision == SHASTA_MIXED ? sweep_warps_per_block_mixed() : sweep_warps_per_block_f32();
+  }
   if (opts.stream) {
     c->stream = (cudaStream_t)opts.stream;
   } else {
@@ -444,10 +527,59 @@ shasta_status shasta_step(shasta_ctx* c, int nsteps) {
   if (nsteps < 0) return fail(c, SHASTA_EINVAL, "nsteps < 0");
   if (!c->state_set) return fail(c, SHASTA_EINVAL, "state not set");
   DeviceGuard dg(c->device);
-  for (int s = 0; s < nsteps; ++s) {
-    int ph = (int)((c->steps) % 6);
+  if (!c->tuned && c->o.autotune && nsteps > 0) {
+    shasta_status st = autotune(c);
+    if (st != SHASTA_OK) return st;
+  }
+  while (nsteps > 0) {
+    if (c->o.use_graphs && nsteps >= 6 && c->steps % 6 == 0 && c->cur == 0) {
+      // six steps (18 sweeps) bring phase and buffer back: one graph
+      if (!c->graph) {
+        cudaGraph_t gr = nullptr;
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        cudaError_t ce = cudaSuccess;
+        for (int s = 0; s < 6 && ce == cudaSuccess; ++s)
+          for (int sub = 0; sub < 3 && ce == cudaSuccess; ++sub) ce = launch_sweep(c, kAxisTable[3 * s + sub]);
+        cudaError_t ce2 = cudaStreamEndCapture(c->stream, &gr);
+        c->cur = 0;
+        if (ce != cudaSuccess || ce2 != cudaSuccess) {
+          if (gr) cudaGraphDestroy(gr);
+          return cuda_fail(c, ce != cudaSuccess ? ce : ce2, "capture six steps");
+        }
+        ce = cudaGraphInstantiate(&c->graph, gr, 0);
+        cudaGraphDestroy(gr);
+        if (ce != cudaSuccess) {
+          c->graph = nullptr;
+          return cuda_fail(c, ce, "cudaGraphInstantiate");
+        }
+      }
+      CK(cudaGraphLaunch(c->graph, c->stream), "cudaGraphLaunch");
+      c->steps += 6;
+      nsteps -= 6;
+      continue;
+    }
+    int ph = (int)(c->steps % 6);
     for (int sub = 0; sub < 3; ++sub) CK(launch_sweep(c, kAxisTable[3 * ph + sub]), "sweep launch");
     ++c->steps;
+    --nsteps;
+  }
+  return SHASTA_OK;
+}
+
+shasta_status shasta_autotune(shasta_ctx* c) {
+  if (!c) return SHASTA_EINVAL;
+  if (!c->state_set) return fail(c, SHASTA_EINVAL, "state not set");
+  DeviceGuard dg(c->device);
+  return autotune(c);
+}
+
+shasta_status shasta_get_tuning(const shasta_ctx* c, int out[6]) {
+  if (!c || !out) return SHASTA_EINVAL;
+  for (int a = 0; a < 3; ++a) {
+    int v, ns;
+    launch_choice(c, a, v, ns);
+    out[2 * a] = v;
+    out[2 * a + 1] = ns;
   }
   return SHASTA_OK;
 }

@@ -14,9 +14,13 @@ namespace shasta {
 cudaError_t launch_sweep_f64(const SweepParams& P, int axis, int eos, cudaStream_t s);
 cudaError_t launch_sweep_f32(const SweepParams& P, int axis, int eos, cudaStream_t s);
 cudaError_t launch_sweep_mixed(const SweepParams& P, int axis, int eos, cudaStream_t s);
-// Resident warps per SM of the FP32 / mixed sweep kernels (launch variant).
-int sweep_warps_per_sm_f32(int axis, int variant);
-int sweep_warps_per_sm_mixed(int axis, int variant);
+// Sets the shared-memory attribute of every FP32 / mixed sweep kernel and
+// reports resident warps per SM as [eos][axis][variant].  Call once per
+// device before the first launch (and before any stream capture).
+cudaError_t prepare_sweep_f32(int occupancy[2][3][2]);
+cudaError_t prepare_sweep_mixed(int occupancy[2][3][2]);
+int sweep_warps_per_block_f32();
+int sweep_warps_per_block_mixed();
 
 // Where the five fields of a state live: element i of field k is at
 // p[k] + i * s[k] (in elements of the storage type).  FP64 states are five

@@ -61,7 +61,8 @@ struct SweepParams {
   unsigned long long* clamp_count;  // cells recovered with |M| clamped or E <= 0
   int seg_len;                      // fast kernels: cells per line segment (multiple of 8)
   int nseg;                         // fast kernels: segments per line
-  int variant;                      // fast kernels: launch variant (0: 3 CTAs/SM, 1: 2 CTAs/SM)
+  int variant;                      // fast kernels: launch variant (0: capped registers, 1: not)
+  long long blocks;                 // fast kernels: grid size (one wave of resident warps)
   // fast kernels: state as (E, Mx, My, Mz) quads per cell plus an R array
   const float* qin;
   const float* rin;

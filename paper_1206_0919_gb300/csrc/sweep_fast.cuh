@@ -37,6 +37,10 @@
 //    p = D/(E + s), v = M/(E + p).  MIXED evaluates D in double-float
 //    (error-free products and sums on the FP32 pipe), which removes the
 //    cancellation as v -> 1 at about FP64 accuracy of D.
+//  * The including units are built with -fmad=false: every fused
+//    multiply-add is explicit, so all instantiations of the streaming step
+//    (position parity, boundary variant, register variant) round alike and
+//    the result does not depend on how lines are cut into segments.
 #pragma once
 
 #include <type_traits>
@@ -179,30 +183,33 @@ __device__ __forceinline__ void copy_cell(const SweepParams& P, float* dq, float
 
 // ----------------------------------------------------------- recovery ----
 
-// Velocity along the sweep and pressure, FP32 (MIXED: D in double-float).
-// m1 is the momentum along the sweep.  Returns 1 if |M| was clamped or
-// E <= 0, else 0.
+// Velocity along the sweep and pressure of one cell, FP32 (MIXED: D in
+// double-float).  mx, my, mz are the momenta, m1 the one along the sweep.
+// For an unclamped cell with the ideal gas this evaluates exactly the
+// expressions of the packed routine below, so a cell's result never depends
+// on the cell it is paired with.  Returns 1 if |M| was clamped or E <= 0.
 template <int EOS, bool MIXED>
-__device__ __forceinline__ unsigned rec32(float E, float m1, float m2, float m3, float omd,
-                                          float B, float ec, float& w, float& p) {
+__device__ __forceinline__ unsigned rec32(float E, float mx, float my, float mz, float m1,
+                                          float omd, float B, float ec, float& w, float& p) {
   unsigned clamped = 0;
-  float M2 = fmaf(m1, m1, fmaf(m2, m2, m3 * m3));
+  float M2 = fmaf(mx, mx, fmaf(my, my, mz * mz));
   const float E2 = E * E;
   const float lim = omd * E;
+  const float L2 = lim * lim;
   float m = m1;
   float D;
-  if (M2 > lim * lim) {
+  if (M2 > L2) {
     // |M| clamped to (1 - delta) E (rare): scale the momentum
     m = m1 * (lim * rsqrtf(M2));
-    M2 = lim * lim;
-    D = fmaf(E, E, -M2);
+    M2 = L2;
+    D = E2 - M2;
     clamped = 1;
   } else if (MIXED) {
-    // D = E^2 - m1^2 - m2^2 - m3^2 from exact products and compensated sums
+    // D = E^2 - mx^2 - my^2 - mz^2 from exact products and compensated sums
     const float e_l = fmaf(E, E, -E2);
-    const float a = m1 * m1, a_l = fmaf(m1, m1, -a);
-    const float b = m2 * m2, b_l = fmaf(m2, m2, -b);
-    const float c = m3 * m3, c_l = fmaf(m3, m3, -c);
+    const float a = mx * mx, a_l = fmaf(mx, mx, -a);
+    const float b = my * my, b_l = fmaf(my, my, -b);
+    const float c = mz * mz, c_l = fmaf(mz, mz, -c);
     const float s1 = E2 - a;
     float bb = s1 - E2;
     const float r1 = (E2 - (s1 - bb)) + (-a - bb);
@@ -214,11 +221,11 @@ __device__ __forceinline__ unsigned rec32(float E, float m1, float m2, float m3,
     const float r3 = (s2 - (s3 - bb)) + (-c - bb);
     D = s3 + (((r1 + r2) + r3) + (((e_l - a_l) - b_l) - c_l));
   } else {
-    D = fmaf(E, E, -M2);
+    D = E2 - M2;
   }
   D = fmaxf(D, 0.0f);
   const float s = sqrtf(fmaf(3.0f, D, E2));
-  float pp = __fdividef(D, E + s);
+  float pp = D * __fdividef(1.0f, E + s);
   if (EOS == EOS_BAG) {
     if (3.0f * pp > ec) {
       const float r = 4.0f * (E - B) * (E - B) - 3.0f * M2;
@@ -233,7 +240,7 @@ __device__ __forceinline__ unsigned rec32(float E, float m1, float m2, float m3,
       if (!ok) pp = __fdividef(M2, E - ec) - E;
     }
   }
-  w = __fdividef(m, E + pp);
+  w = m * __fdividef(1.0f, E + pp);
   p = pp;
   if (!(E > 0.0f)) {
     w = 0.0f;
@@ -247,16 +254,17 @@ __device__ __forceinline__ unsigned rec32(float E, float m1, float m2, float m3,
 // and the momentum along the sweep, packed.  Clamped or vacuum cells, the
 // bag EoS and MIXED take the scalar routine.  Returns the lo clamp flag.
 template <int EOS, bool MIXED>
-__device__ __forceinline__ unsigned rec2(f2 E, f2 mx, f2 my, f2 mz, f2 mpar, f2 mt1, f2 mt2,
-                                         f2 omd2, float omd, float B, float ec, f2& w, f2& p) {
+__device__ __forceinline__ unsigned rec2(f2 E, f2 mx, f2 my, f2 mz, f2 mpar, f2 omd2, float omd,
+                                         float B, float ec, f2& w, f2& p) {
   auto scalar = [&]() -> unsigned {
-    float El, Eh, al, ah, bl, bh, cl, ch, wl, wh_, pl, ph;
+    float El, Eh, xl, xh, yl, yh, zl, zh, al, ah, wl, wh_, pl, ph;
     up(E, El, Eh);
+    up(mx, xl, xh);
+    up(my, yl, yh);
+    up(mz, zl, zh);
     up(mpar, al, ah);
-    up(mt1, bl, bh);
-    up(mt2, cl, ch);
-    const unsigned c = rec32<EOS, MIXED>(El, al, bl, cl, omd, B, ec, wl, pl);
-    rec32<EOS, MIXED>(Eh, ah, bh, ch, omd, B, ec, wh_, ph);
+    const unsigned c = rec32<EOS, MIXED>(El, xl, yl, zl, al, omd, B, ec, wl, pl);
+    rec32<EOS, MIXED>(Eh, xh, yh, zh, ah, omd, B, ec, wh_, ph);
     w = pk(wl, wh_);
     p = pk(pl, ph);
     return c;
@@ -385,15 +393,18 @@ __device__ __forceinline__ void init1(Line1& s) {
 }
 
 // Transport coefficients of cell k-1 from w_{k-1}, w_k and Q+_{k-2}:
-// Q+ of Eq. shasta-diff and Q-_{k-1} = 1 - Q+_{k-2}.
+// Q+ of Eq. shasta-diff and Q-_{k-1} = 1 - Q+_{k-2}.  Every fused
+// multiply-add is written out (the unit is built without contraction), so
+// each instantiation of the streaming step rounds identically.
 __device__ __forceinline__ void coeffs(float tau, float w1, float w0, float& qprev, float& a,
                                        float& nb, float& c) {
-  const float e1 = tau * w1, e0 = tau * w0;
-  const float qp = __fdividef(0.5f - e1, 1.0f + (e0 - e1));
+  const float num = fmaf(-tau, w1, 0.5f);          // 1/2 - eps_{k-1}
+  const float den = fmaf(tau, w0 - w1, 1.0f);      // 1 + (eps_k - eps_{k-1})
+  const float qp = num * __fdividef(1.0f, den);
   const float qm = 1.0f - qprev;
   qprev = qp;
-  a = 0.5f * qp * qp;
-  nb = -0.5f * qm * qm;
+  a = 0.5f * (qp * qp);
+  nb = -0.5f * (qm * qm);
   c = qp + qm;
 }
 
@@ -587,10 +598,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParam
       const f2 my = pk(lo_of(uB), lo_of(HB));
       const f2 mz = pk(hi_of(uB), hi_of(HB));
       const f2 mpar = AXIS == 0 ? mx : (AXIS == 1 ? my : mz);
-      const f2 mt1 = AXIS == 0 ? my : mx;
-      const f2 mt2 = AXIS == 2 ? my : mz;
       f2 w2, p2;
-      const unsigned c0 = rec2<EOS, MIXED>(E, mx, my, mz, mpar, mt1, mt2, omd2, omd, B, ec, w2, p2);
+      const unsigned c0 = rec2<EOS, MIXED>(E, mx, my, mz, mpar, omd2, omd, B, ec, w2, p2);
       nclamp += ((unsigned)(q - s0) < (unsigned)(s1 - s0)) ? c0 : 0u;
       float pl, phi, pwl, pwh;
       up(w2, wn0, wh0);

@@ -1,4 +1,6 @@
 // sweep_mixed.cu -- MIXED: state, transport and limiter in float; the recovery's E^2 - |M|^2 in double-float.
+#include <mutex>
+
 #include "kernels.h"
 #include "sweep_fast.cuh"
 
@@ -9,66 +11,57 @@ namespace {
 constexpr int kWarps = 4, kRing = 8, kDist = 3;
 
 template <int EOS, int AXIS, int MINB>
-cudaError_t go2(const SweepParams& P, cudaStream_t s) {
-  auto k = fast::sweep_fast_kernel<EOS, AXIS, true, kWarps, kRing, kDist, MINB>;
-  const size_t smem = (size_t)kWarps * fast::Smem<AXIS, kRing>::per_warp * sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  // one wave of resident warps loops over the (line group, segment) items
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kWarps * 32, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
-  const long long items = ((P.plane + 31) / 32) * P.nseg;
-  long long blocks = (items + kWarps - 1) / kWarps;
-  const long long wave = (long long)sms * per_sm;
-  if (blocks > wave) blocks = wave;
-  k<<<(unsigned)blocks, kWarps * 32, smem, s>>>(P);
-  return cudaGetLastError();
-}
-
-// variant 0: registers capped for 3 CTAs (12 warps) per SM; 1: uncapped.
-template <int EOS, int AXIS>
-cudaError_t go(const SweepParams& P, cudaStream_t s) {
-  return P.variant == 1 ? go2<EOS, AXIS, 1>(P, s) : go2<EOS, AXIS, 3>(P, s);
+void* kfun() {
+  return (void*)fast::sweep_fast_kernel<EOS, AXIS, true, kWarps, kRing, kDist, MINB>;
 }
 
 template <int AXIS>
-int resident_warps_per_sm(int variant) {
-  auto k0 = fast::sweep_fast_kernel<EOS_IDEAL, AXIS, true, kWarps, kRing, kDist, 3>;
-  auto k1 = fast::sweep_fast_kernel<EOS_IDEAL, AXIS, true, kWarps, kRing, kDist, 1>;
-  const size_t smem = (size_t)kWarps * fast::Smem<AXIS, kRing>::per_warp * sizeof(float);
-  int per_sm = 0;
-  if (variant == 1) {
-    cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k1, kWarps * 32, smem);
-  } else {
-    cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k0, kWarps * 32, smem);
-  }
-  return per_sm * kWarps;
+size_t smem_bytes() {
+  return (size_t)kWarps * fast::Smem<AXIS, kRing>::per_warp * sizeof(float);
 }
+
+// kernel of (eos, axis, variant); variant 0: registers capped for 3 CTAs
+// (12 warps) per SM, 1: uncapped
+void* kernel_of(int eos, int axis, int variant) {
+  static void* const table[2][3][2] = {
+      {{kfun<EOS_IDEAL, 0, 3>(), kfun<EOS_IDEAL, 0, 1>()},
+       {kfun<EOS_IDEAL, 1, 3>(), kfun<EOS_IDEAL, 1, 1>()},
+       {kfun<EOS_IDEAL, 2, 3>(), kfun<EOS_IDEAL, 2, 1>()}},
+      {{kfun<EOS_BAG, 0, 3>(), kfun<EOS_BAG, 0, 1>()},
+       {kfun<EOS_BAG, 1, 3>(), kfun<EOS_BAG, 1, 1>()},
+       {kfun<EOS_BAG, 2, 3>(), kfun<EOS_BAG, 2, 1>()}}};
+  return table[eos][axis][variant];
+}
+
+size_t smem_of(int axis) { return axis == 0 ? smem_bytes<0>() : (axis == 1 ? smem_bytes<1>() : smem_bytes<2>()); }
 
 }  // namespace
 
-int sweep_warps_per_sm_mixed(int axis, int variant) {
-  return axis == 0 ? resident_warps_per_sm<0>(variant)
-                   : (axis == 1 ? resident_warps_per_sm<1>(variant) : resident_warps_per_sm<2>(variant));
+cudaError_t prepare_sweep_mixed(int occupancy[2][3][2]) {
+  for (int eos = 0; eos < 2; ++eos)
+    for (int axis = 0; axis < 3; ++axis)
+      for (int var = 0; var < 2; ++var) {
+        const void* k = kernel_of(eos, axis, var);
+        const size_t smem = smem_of(axis);
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kWarps * 32, smem);
+        if (e != cudaSuccess) return e;
+        occupancy[eos][axis][var] = per_sm * kWarps;
+      }
+  return cudaSuccess;
 }
 
 cudaError_t launch_sweep_mixed(const SweepParams& P, int axis, int eos, cudaStream_t s) {
   if (P.plane <= 0) return cudaSuccess;
-  switch (eos * 3 + axis) {
-    case 0: return go<EOS_IDEAL, 0>(P, s);
-    case 1: return go<EOS_IDEAL, 1>(P, s);
-    case 2: return go<EOS_IDEAL, 2>(P, s);
-    case 3: return go<EOS_BAG, 0>(P, s);
-    case 4: return go<EOS_BAG, 1>(P, s);
-    case 5: return go<EOS_BAG, 2>(P, s);
-  }
-  return cudaErrorInvalidValue;
+  if (axis < 0 || axis > 2 || eos < 0 || eos > 1 || P.variant < 0 || P.variant > 1 || P.blocks < 1)
+    return cudaErrorInvalidValue;
+  void* args[] = {const_cast<SweepParams*>(&P)};
+  return cudaLaunchKernel(kernel_of(eos, axis, P.variant), dim3((unsigned)P.blocks), dim3(kWarps * 32),
+                          args, smem_of(axis), s);
 }
+
+int sweep_warps_per_block_mixed() { return kWarps; }
 
 }  // namespace shasta

@@ -45,7 +45,8 @@ class Eos(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("eta", C.c_double), ("delta", C.c_double),
-                ("stream", C.c_void_p), ("device", C.c_int), ("check_input", C.c_int)]
+                ("stream", C.c_void_p), ("device", C.c_int), ("check_input", C.c_int),
+                ("autotune", C.c_int), ("use_graphs", C.c_int)]
 
 
 _lock = threading.Lock()
@@ -65,6 +66,8 @@ SIGNATURES = {
     "shasta_step": (C.c_int, [_vp, C.c_int]),
     "shasta_sweep": (C.c_int, [_vp, C.c_int]),
     "shasta_sync": (C.c_int, [_vp]),
+    "shasta_autotune": (C.c_int, [_vp]),
+    "shasta_get_tuning": (C.c_int, [_vp, C.POINTER(C.c_int)]),
     "shasta_get_conserved": (C.c_int, [_vp] + [_vp] * 5 + [C.c_int]),
     "shasta_get_primitives": (C.c_int, [_vp] + [_vp] * 6 + [C.c_int]),
     "shasta_totals": (C.c_int, [_vp, _dp]),
@@ -149,7 +152,7 @@ class Solver:
 
     def __init__(self, shape, lam=0.4, dx=1.0, precision="fp32", bc="reflect", eos="ideal",
                  bag_B=0.1, bag_ec=0.5, eta=0.125, delta=0.0, stream=None, device=0,
-                 check_input=True):
+                 check_input=True, autotune=True, use_graphs=True):
         L = lib()
         nx, ny, nz = shape
         self.shape = (nx, ny, nz)
@@ -164,6 +167,8 @@ class Solver:
         o.stream = stream
         o.device = device
         o.check_input = 1 if check_input else 0
+        o.autotune = 1 if autotune else 0
+        o.use_graphs = 1 if use_graphs else 0
         h = _vp()
         _check(L.shasta_create(C.byref(g), dx, lam, C.byref(e), C.byref(o), C.byref(h)))
         self._h = h
@@ -208,6 +213,14 @@ class Solver:
 
     def sweep(self, axis):
         _check(lib().shasta_sweep(self._h, int(axis)), self._h)
+
+    def autotune(self):
+        _check(lib().shasta_autotune(self._h), self._h)
+
+    def tuning(self):
+        out = (C.c_int * 6)()
+        _check(lib().shasta_get_tuning(self._h, out), self._h)
+        return [(out[2 * a], out[2 * a + 1]) for a in range(3)]
 
     def sync(self):
         _check(lib().shasta_sync(self._h), self._h)

@@ -235,3 +235,45 @@ def test_clamp_counter():
             s.set_conserved(bad)
             s.sweep(0)
             assert s.counters() >= 1
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed", "fp64"])
+def test_graphs_and_launch_choices_bitwise(monkeypatch, precision):
+    """CUDA-graph replay, the autotuner and every forced launch choice
+    (segments per line, register variant) give bitwise identical states."""
+    shape = (72, 56, 48)
+    pr = W.hot_spots(shape=shape, seed=21, n_spots=6, sigma=(2.0, 4.0), radial_flow=0.1)
+    O = oracle()
+    U0 = O.prim2cons(OR.params(shape), *pr.as_list())
+
+    def run(**kw):
+        with S.Solver(shape, precision=precision, **kw) as s:
+            s.set_conserved(U0)
+            s.step(13)  # two graph replays of six steps + one single step
+            return s.get_conserved()
+
+    ref = run(autotune=False, use_graphs=False)
+    outs = [run(autotune=True, use_graphs=True)]
+    if precision != "fp64":
+        for nseg, var in ((1, 0), (3, 1), (4, 0)):
+            monkeypatch.setenv("SHASTA_NSEG", str(nseg))
+            monkeypatch.setenv("SHASTA_VARIANT", str(var))
+            outs.append(run(autotune=False, use_graphs=True))
+    for out in outs:
+        for a, b in zip(ref, out):
+            assert np.array_equal(a, b)
+
+
+def test_autotune_keeps_state():
+    shape = (64, 48, 40)
+    pr = W.hot_spots(shape=shape, seed=22, n_spots=4)
+    U0 = oracle().prim2cons(OR.params(shape), *pr.as_list())
+    with S.Solver(shape, precision="fp32", autotune=False) as s:
+        s.set_conserved(U0)
+        before = s.get_conserved()
+        s.autotune()
+        after = s.get_conserved()
+        tune = s.tuning()
+    for a, b in zip(before, after):
+        assert np.array_equal(a, b)
+    assert all(v in (0, 1) and ns >= 1 for v, ns in tune)
