@@ -29,6 +29,7 @@
 #ifndef SHASTA_H
 #define SHASTA_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -168,6 +169,46 @@ shasta_status shasta_get_primitives(shasta_ctx* ctx, double* e, double* vx, doub
  * device with a fixed reduction order (deterministic).  out: 5 host doubles.
  * Synchronous. */
 shasta_status shasta_totals(shasta_ctx* ctx, double out[5]);
+
+/* Totals without allocation (the paper has no counterpart: this is a
+ * service for callers that cannot allocate device memory).
+ *
+ * Some callers cannot call cudaMalloc where they need the totals: code that
+ * runs under another framework's device-memory pool, where a raw allocation
+ * would escape its accounting or synchronise the device, and code that is
+ * forbidden to allocate once it has started.  This call sums caller-owned
+ * fields and allocates nothing; its per-block partial sums live in a fixed
+ * array of 5 * SHASTA_TOTALS_NOALLOC_MAX_CELLS /
+ * SHASTA_TOTALS_NOALLOC_CELLS_PER_BLOCK doubles (320 KiB) inside the
+ * library's device code, which every GPU that loads the library holds until
+ * the process exits.
+ *
+ * E, Mx, My, Mz, R: device pointers to n doubles each on the calling
+ * thread's current device (any layout, summed as flat arrays).  out: device
+ * pointer to 5 doubles, written with the sums of E, Mx, My, Mz, R in a fixed
+ * reduction order (deterministic for a given n; the order differs from
+ * shasta_totals', so the two agree to rounding).  stream: a cudaStream_t of
+ * that device, NULL for the legacy default stream.  The work is enqueued and
+ * the call returns without waiting; out is ready when the stream reaches it.
+ * The caller keeps ownership of every pointer.
+ *
+ * The first call on a device looks up the address of the fixed array on
+ * that device (it may load the library's device code there); make that
+ * first call before any stream capture on the device.  All calls on a device
+ * share the array, which keeps the last call's partials: each call writes
+ * every partial it reads, so nothing needs clearing, but calls whose work
+ * overlaps on the GPU (two streams, or two threads) race on the array and
+ * must be ordered by the caller.
+ *
+ * Errors: EINVAL (out NULL, a field NULL with n > 0, n larger than
+ * SHASTA_TOTALS_NOALLOC_MAX_CELLS, or a device ordinal of 64 or more),
+ * ECUDA (no current device, the address lookup or a launch failed).  No
+ * message is kept: the status is the whole report. */
+#define SHASTA_TOTALS_NOALLOC_MAX_CELLS 67108864ull /* 2^26 cells, e.g. 406^3 */
+#define SHASTA_TOTALS_NOALLOC_CELLS_PER_BLOCK 8192ull
+shasta_status shasta_totals_noalloc(const double* E, const double* Mx, const double* My,
+                                    const double* Mz, const double* R, size_t n, double* out,
+                                    void* stream);
 
 /* Number of full steps taken since the state was last set (the permutation
  * phase is this mod 6). */

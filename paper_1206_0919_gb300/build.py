@@ -31,6 +31,7 @@ FAST = ["-fmad=false", "-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
 UNITS = [
     ("api.cu", EXACT),
     ("aux.cu", EXACT),
+    ("noalloc.cu", EXACT),
     ("sweep_f64.cu", EXACT),
     ("sweep_f32.cu", FAST),
     ("sweep_mixed.cu", FAST),

@@ -319,6 +319,22 @@ cudaError_t launch_totals(const FieldView& f, size_t n, int is32, double* partia
   return cudaGetLastError();
 }
 
+cudaError_t launch_totals_chunked(const FieldView& f, size_t n, int is32, size_t chunk, int nb,
+                                  double* partials, double* out, cudaStream_t s) {
+  Tot5 p;
+  p.f = f;
+  if (nb > 0) {
+    if (is32)
+      k_totals_partial<float><<<nb, kTotThreads, 0, s>>>(p, n, chunk, partials);
+    else
+      k_totals_partial<double><<<nb, kTotThreads, 0, s>>>(p, n, chunk, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  k_totals_final<<<1, kTotThreads, 0, s>>>(partials, nb, out);
+  return cudaGetLastError();
+}
+
 size_t frozen_axis_offset(int nx, int ny, int nz, int axis) {
   size_t planes[3] = {(size_t)ny * nz, (size_t)nx * nz, (size_t)nx * ny};
   size_t off = 0;

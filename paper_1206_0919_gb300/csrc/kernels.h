@@ -58,6 +58,10 @@ cudaError_t launch_check_prims(const double* const f[5], size_t n, unsigned long
 int totals_blocks(size_t n);
 cudaError_t launch_totals(const FieldView& f, size_t n, int is32, double* partials, double* out,
                           cudaStream_t s);
+// The same two-pass totals with an explicit chunk per block and block count
+// nb (partials: 5 * nb doubles of scratch).
+cudaError_t launch_totals_chunked(const FieldView& f, size_t n, int is32, size_t chunk, int nb,
+                                  double* partials, double* out, cudaStream_t s);
 // Frozen ghost store: for each axis a block [side][layer][field][plane].
 size_t frozen_elems(int nx, int ny, int nz);
 size_t frozen_axis_offset(int nx, int ny, int nz, int axis);

@@ -71,6 +71,7 @@ SIGNATURES = {
     "shasta_get_conserved": (C.c_int, [_vp] + [_vp] * 5 + [C.c_int]),
     "shasta_get_primitives": (C.c_int, [_vp] + [_vp] * 6 + [C.c_int]),
     "shasta_totals": (C.c_int, [_vp, _dp]),
+    "shasta_totals_noalloc": (C.c_int, [_vp] * 5 + [C.c_size_t, _vp, _vp]),
     "shasta_steps_done": (C.c_int64, [_vp]),
     "shasta_set_step_counter": (C.c_int, [_vp, C.c_int64]),
     "shasta_counters": (C.c_int, [_vp, C.POINTER(C.c_int64)]),
@@ -145,6 +146,40 @@ def _ptrs(arrays):
         return [None if a is None else _host_ptr(a) for a in keep], MEM_HOST, keep
     keep = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in arrays]
     return [None if a is None else _host_ptr(a) for a in keep], MEM_HOST, keep
+
+
+TOTALS_NOALLOC_MAX_CELLS = 1 << 26
+
+
+def totals_noalloc(E, Mx, My, Mz, R, out, stream=None):
+    """Sums of five caller-owned device fields into the caller's device
+    tensor ``out`` (5 float64) without any device allocation, for callers
+    that cannot allocate (see ``shasta_totals_noalloc``).  The fields are
+    contiguous float64 CUDA tensors of one size on the current device;
+    ``stream`` is a torch.cuda.Stream or raw cudaStream_t (default: torch's
+    current stream).  Enqueues and returns without waiting."""
+    import torch
+    fields = (E, Mx, My, Mz, R)
+    n = E.numel()
+    for a in fields + (out,):
+        if not (a.is_cuda and a.dtype == torch.float64 and a.is_contiguous()):
+            raise ValueError("fields and out must be contiguous float64 CUDA tensors")
+    if any(a.numel() != n for a in fields) or out.numel() < 5:
+        raise ValueError("fields must have one size and out at least 5 elements")
+    if n > TOTALS_NOALLOC_MAX_CELLS:
+        raise ShastaError(EINVAL, f"{n} cells exceed the fixed scratch limit of "
+                                  f"{TOTALS_NOALLOC_MAX_CELLS} cells of shasta_totals_noalloc")
+    if stream is None:
+        stream = torch.cuda.current_stream(E.device).cuda_stream
+    elif not isinstance(stream, int):
+        stream = stream.cuda_stream
+    with torch.cuda.device(E.device):  # the call works on the current device
+        st = lib().shasta_totals_noalloc(*[a.data_ptr() for a in fields], n, out.data_ptr(),
+                                         stream)
+    if st != OK:
+        raise ShastaError(st, "shasta_totals_noalloc failed"
+                          + (" (more cells than its fixed scratch holds, or a NULL pointer)"
+                             if st == EINVAL else ""))
 
 
 class Solver:
