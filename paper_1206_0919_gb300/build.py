@@ -32,9 +32,12 @@ UNITS = [
     ("api.cu", EXACT),
     ("aux.cu", EXACT),
     ("noalloc.cu", EXACT),
+    ("batch.cu", EXACT),
     ("sweep_f64.cu", EXACT),
     ("sweep_f32.cu", FAST),
     ("sweep_mixed.cu", FAST),
+    ("batch_f32.cu", FAST),
+    ("batch_mixed.cu", FAST),
 ]
 
 

@@ -1,0 +1,934 @@
+// batch.cu -- the C ABI of include/shasta_batch.h: many events in one device
+// pool, advanced by one batched launch per (sweep slot, axis, EoS) group.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/shasta_batch.h"
+#include "kernels.h"
+
+using namespace shasta;
+
+namespace {
+
+thread_local std::string g_batch_create_error;
+
+// Fixed permutation of the sweep axes, Sec. 3.1.4 (as in the single-event
+// path).
+const int kAxisTable[18] = {0, 1, 2, 0, 2, 1, 2, 0, 1, 2, 1, 0, 1, 2, 0, 1, 0, 2};
+
+constexpr long long kAlign = 32;  // cells: every event starts on a 512-byte quad boundary
+constexpr int kTotBlocks = 1024;  // partial sums of the totals reduction
+
+// First-fit allocator of cell ranges [0, cap) with coalescing frees.
+class RangeAlloc {
+ public:
+  void reset(long long cap) {
+    free_.clear();
+    if (cap > 0) free_[0] = cap;
+  }
+  // Start of a free range of len cells (aligned to kAlign), or -1.
+  long long alloc(long long len) {
+    len = (len + kAlign - 1) / kAlign * kAlign;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= len) {
+        const long long start = it->first, rest = it->second - len;
+        free_.erase(it);
+        if (rest > 0) free_[start + len] = rest;
+        return start;
+      }
+    }
+    return -1;
+  }
+  void release(long long start, long long len) {
+    len = (len + kAlign - 1) / kAlign * kAlign;
+    auto nx = free_.lower_bound(start);
+    if (nx != free_.end() && start + len == nx->first) {
+      len += nx->second;
+      nx = free_.erase(nx);
+    }
+    if (nx != free_.begin()) {
+      auto pv = std::prev(nx);
+      if (pv->first + pv->second == start) {
+        pv->second += len;
+        return;
+      }
+    }
+    free_[start] = len;
+  }
+  long long largest() const {
+    long long m = 0;
+    for (auto& kv : free_) m = std::max(m, kv.second);
+    return m;
+  }
+
+ private:
+  std::map<long long, long long> free_;
+};
+
+struct Event {
+  bool live = false;
+  shasta_grid g{};
+  double lambda = 0.4;
+  shasta_eos eos{};
+  long long off = 0;
+  long long ncell = 0;
+  int64_t steps = 0;
+  void* frozen = nullptr;
+};
+
+// One batched launch of a plan: the events of list entries [idx_off, +nlist)
+// of the device plan array, swept along `axis`.
+struct LaunchRec {
+  int axis = 0, eos = 0, nlist = 0;
+  size_t idx_off = 0, pre_off = 0;
+  long long items = 0;
+};
+
+}  // namespace
+
+struct shasta_batch {
+  int device = 0;
+  shasta_batch_opts o{};
+  bool mixed = false;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  long long cap = 0;
+  void* pool = nullptr;
+  float* quad[2] = {};
+  float* rf[2] = {};
+  int cur = 0;
+  RangeAlloc cells;
+  std::vector<Event> ev;
+  int nlive = 0;
+  long long used = 0;
+  EvDesc* d_desc = nullptr;
+  EvDesc* h_desc = nullptr;  // pinned
+  unsigned long long* d_count = nullptr;  // per slot clamp counters; [max_events] check scratch
+  int* d_plan = nullptr;
+  size_t plan_cap = 0;  // ints
+  int* h_plan = nullptr;  // pinned
+  size_t h_plan_cap = 0;
+  double* staging = nullptr;
+  size_t staging_cells = 0;
+  double* partials = nullptr;
+  double* d_tot = nullptr;
+  double* h_small = nullptr;  // pinned
+  int sm_count = 152;
+  int occ[2][3][2] = {};
+  int wpb = 4;
+  // launch choice per axis: register variant and target segment length
+  // (0: lines are not split)
+  bool tuned = false;
+  int tune_var[3] = {0, 0, 0};
+  int tune_len[3] = {0, 0, 0};
+  // work lists of six consecutive steps (index (steps - plan_base) mod 6)
+  bool plan_valid = false;
+  int64_t bsteps = 0, plan_base = 0;
+  std::vector<LaunchRec> plan[6][3];
+  cudaGraphExec_t graph = nullptr;
+  int graph_r = -1, graph_cur = -1;
+  std::string err;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int now = -1;
+    if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+  }
+};
+
+shasta_status fail(shasta_batch* b, shasta_status s, const std::string& msg) {
+  if (b)
+    b->err = msg;
+  else
+    g_batch_create_error = msg;
+  return s;
+}
+
+shasta_status cuda_fail(shasta_batch* b, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return fail(b, e == cudaErrorMemoryAllocation ? SHASTA_ENOMEM : SHASTA_ECUDA, m);
+}
+
+#define CK(call, where)                                    \
+  do {                                                     \
+    cudaError_t _e = (call);                               \
+    if (_e != cudaSuccess) return cuda_fail(b, _e, where); \
+  } while (0)
+
+int extent(const shasta_grid& g, int axis) { return axis == 0 ? g.nx : (axis == 1 ? g.ny : g.nz); }
+
+long long plane_of(const shasta_grid& g, int axis) {
+  return axis == 0 ? (long long)g.ny * g.nz
+                   : (axis == 1 ? (long long)g.nx * g.nz : (long long)g.nx * g.ny);
+}
+
+// Segments per line for a target segment length (0: one segment); at
+// least 16 cells per segment.
+int nseg_for(int n, int len) {
+  if (len <= 0) return 1;
+  int k = (n + len / 2) / len;
+  const int kmax = n / 16 > 1 ? n / 16 : 1;
+  return std::max(1, std::min(k, kmax));
+}
+
+long long groups_of(const Event& e, int axis) { return (plane_of(e.g, axis) + 31) / 32; }
+
+// Resident warps of the machine for a launch choice.
+long long warp_slots(const shasta_batch* b, int eos, int axis, int var) {
+  const int w = b->occ[eos][axis][var];
+  return (long long)b->sm_count * (w > 0 ? w : 1);
+}
+
+// Model of the makespan of one axis over all events for a target segment
+// length: total line positions spread over the resident warps, plus the
+// longest item (the tail); each segment pays a 13-position halo and lag.
+double model_cost(const shasta_batch* b, int axis, int len) {
+  double work = 0, tail = 0;
+  for (const Event& e : b->ev) {
+    if (!e.live) continue;
+    const int n = extent(e.g, axis);
+    const int k = nseg_for(n, len);
+    work += (double)groups_of(e, axis) * (n + 13.0 * k);
+    tail = std::max(tail, (double)n / k + 13.0);
+  }
+  return work / (double)warp_slots(b, 0, axis, 0) + tail;
+}
+
+void model_choice(shasta_batch* b) {
+  static const int cands[] = {0, 128, 96, 64, 48, 32};
+  for (int a = 0; a < 3; ++a) {
+    double best = 1e300;
+    int bl = 0;
+    for (int len : cands) {
+      const double c = model_cost(b, a, len);
+      if (c < best * 0.999) {
+        best = c;
+        bl = len;
+      }
+    }
+    b->tune_var[a] = 0;
+    b->tune_len[a] = bl;
+  }
+}
+
+FieldView view_of(const shasta_batch* b, const Event& e, int buf) {
+  FieldView v;
+  for (int k = 0; k < 4; ++k) {
+    v.p[k] = b->quad[buf] + 4 * e.off + k;
+    v.s[k] = 4;
+  }
+  v.p[4] = b->rf[buf] + e.off;
+  v.s[4] = 1;
+  return v;
+}
+
+EosParams eos_params(const shasta_batch* b, const Event& e) {
+  EosParams q;
+  q.kind = e.eos.kind;
+  q.B = e.eos.B;
+  q.ec = e.eos.e_c;
+  q.omd = 1.0 - b->o.delta;
+  return q;
+}
+
+// Descriptor of slot i with the segment counts of the current launch choice
+// (or of `len_override` on axis `ax_override`, for tuning).
+EvDesc desc_of(const shasta_batch* b, int i, int ax_override = -1, int len_override = 0) {
+  const Event& e = b->ev[i];
+  EvDesc d;
+  memset(&d, 0, sizeof d);
+  d.off = e.off;
+  d.nx = e.g.nx;
+  d.ny = e.g.ny;
+  d.nz = e.g.nz;
+  d.bc = e.g.bc;
+  for (int a = 0; a < 3; ++a)
+    d.nseg[a] = nseg_for(extent(e.g, a), a == ax_override ? len_override : b->tune_len[a]);
+  // the same double -> float conversions as the single-event launch
+  const double tau_h = 0.5 * e.lambda, tau_f = e.lambda;
+  d.tau_h = (float)tau_h;
+  d.tau_f = (float)tau_f;
+  d.htau_h = (float)(0.5 * tau_h);
+  d.htau_f = (float)(0.5 * tau_f);
+  d.bag_B = (float)e.eos.B;
+  d.bag_ec = (float)e.eos.e_c;
+  for (int a = 0; a < 3; ++a)
+    d.frozen[a] = e.frozen ? (const float*)e.frozen +
+                                 frozen_axis_offset(e.g.nx, e.g.ny, e.g.nz, a)
+                           : nullptr;
+  d.clamp_count = b->d_count + i;
+  return d;
+}
+
+// Highest live slot + 1.
+int slots_in_use(const shasta_batch* b) {
+  int n = 0;
+  for (int i = 0; i < (int)b->ev.size(); ++i)
+    if (b->ev[i].live) n = i + 1;
+  return n;
+}
+
+// Writes the descriptors of all slots in use (synchronous: the pinned copy
+// is reused).
+shasta_status upload_desc(shasta_batch* b, int ax_override = -1, int len_override = 0) {
+  const int n = slots_in_use(b);
+  if (!n) return SHASTA_OK;
+  CK(cudaStreamSynchronize(b->stream), "sync");
+  for (int i = 0; i < n; ++i)
+    if (b->ev[i].live) b->h_desc[i] = desc_of(b, i, ax_override, len_override);
+  CK(cudaMemcpyAsync(b->d_desc, b->h_desc, n * sizeof(EvDesc), cudaMemcpyHostToDevice, b->stream),
+     "upload descriptors");
+  CK(cudaStreamSynchronize(b->stream), "sync");
+  return SHASTA_OK;
+}
+
+// Appends the work list of events `ids` along `axis` (longest items first)
+// to the host plan array.
+LaunchRec make_list(const shasta_batch* b, std::vector<int>& ids, int axis, int eos, int len_axis,
+                    int len, std::vector<int>& out) {
+  auto item_len = [&](int i) {
+    const int n = extent(b->ev[i].g, axis);
+    return (double)n / nseg_for(n, axis == len_axis ? len : b->tune_len[axis]);
+  };
+  std::stable_sort(ids.begin(), ids.end(), [&](int x, int y) { return item_len(x) > item_len(y); });
+  LaunchRec L;
+  L.axis = axis;
+  L.eos = eos;
+  L.nlist = (int)ids.size();
+  L.idx_off = out.size();
+  for (int i : ids) out.push_back(i);
+  L.pre_off = out.size();
+  long long acc = 0;
+  for (int i : ids) {
+    out.push_back((int)acc);
+    const Event& e = b->ev[i];
+    acc += groups_of(e, axis) * nseg_for(extent(e.g, axis), axis == len_axis ? len : b->tune_len[axis]);
+  }
+  out.push_back((int)acc);
+  L.items = acc;
+  return L;
+}
+
+shasta_status upload_plan(shasta_batch* b, const std::vector<int>& host) {
+  if (host.empty()) return SHASTA_OK;
+  CK(cudaStreamSynchronize(b->stream), "sync");
+  if (host.size() > b->plan_cap) {
+    cudaFree(b->d_plan);
+    b->d_plan = nullptr;
+    b->plan_cap = 0;
+    size_t cap = std::max<size_t>(host.size() * 2, 4096);
+    CK(cudaMalloc((void**)&b->d_plan, cap * sizeof(int)), "cudaMalloc plan");
+    b->plan_cap = cap;
+  }
+  if (host.size() > b->h_plan_cap) {
+    cudaFreeHost(b->h_plan);
+    b->h_plan = nullptr;
+    b->h_plan_cap = 0;
+    size_t cap = std::max<size_t>(host.size() * 2, 4096);
+    CK(cudaMallocHost((void**)&b->h_plan, cap * sizeof(int)), "cudaMallocHost plan");
+    b->h_plan_cap = cap;
+  }
+  memcpy(b->h_plan, host.data(), host.size() * sizeof(int));
+  CK(cudaMemcpyAsync(b->d_plan, b->h_plan, host.size() * sizeof(int), cudaMemcpyHostToDevice,
+                     b->stream),
+     "upload plan");
+  CK(cudaStreamSynchronize(b->stream), "sync");
+  return SHASTA_OK;
+}
+
+void drop_graph(shasta_batch* b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+  b->graph_r = b->graph_cur = -1;
+}
+
+// Work lists of the next six steps: in step r and sweep slot s, event e
+// sweeps along axis kAxisTable[3 ((steps_e + r) mod 6) + s]; the events of
+// one (axis, EoS) share a launch.
+shasta_status build_plan(shasta_batch* b) {
+  std::vector<int> host;
+  const int n = slots_in_use(b);
+  for (int r = 0; r < 6; ++r)
+    for (int s = 0; s < 3; ++s) {
+      b->plan[r][s].clear();
+      std::vector<int> groups[3][2];
+      for (int i = 0; i < n; ++i) {
+        const Event& e = b->ev[i];
+        if (!e.live) continue;
+        const int ph = (int)((e.steps + r) % 6);
+        groups[kAxisTable[3 * ph + s]][e.eos.kind].push_back(i);
+      }
+      for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < 2; ++k)
+          if (!groups[a][k].empty())
+            b->plan[r][s].push_back(make_list(b, groups[a][k], a, k, -1, 0, host));
+    }
+  shasta_status st = upload_desc(b);
+  if (st != SHASTA_OK) return st;
+  st = upload_plan(b, host);
+  if (st != SHASTA_OK) return st;
+  b->plan_base = b->bsteps;
+  b->plan_valid = true;
+  drop_graph(b);
+  return SHASTA_OK;
+}
+
+SweepParams batch_params(const shasta_batch* b, const LaunchRec& L, int from, int variant) {
+  SweepParams P;
+  memset(&P, 0, sizeof P);
+  P.qin = b->quad[from];
+  P.rin = b->rf[from];
+  P.qout = b->quad[from ^ 1];
+  P.rout = b->rf[from ^ 1];
+  P.eta = b->o.eta;
+  P.omd = 1.0 - b->o.delta;
+  P.variant = variant;
+  P.nseg = 1;
+  P.plane = 1;
+  // one wave of resident warps loops over the items
+  const long long wave = warp_slots(b, L.eos, L.axis, variant) / b->wpb;
+  const long long need = (L.items + b->wpb - 1) / b->wpb;
+  P.blocks = std::max(1LL, std::min(need, wave));
+  return P;
+}
+
+cudaError_t launch_rec(shasta_batch* b, const LaunchRec& L, int from, int variant) {
+  if (!L.nlist || !L.items) return cudaSuccess;
+  const SweepParams P = batch_params(b, L, from, variant);
+  BatchList BL;
+  BL.ev = b->d_desc;
+  BL.idx = b->d_plan + L.idx_off;
+  BL.prefix = b->d_plan + L.pre_off;
+  BL.nlist = L.nlist;
+  return b->mixed ? launch_batch_mixed(P, BL, L.axis, L.eos, b->stream)
+                  : launch_batch_f32(P, BL, L.axis, L.eos, b->stream);
+}
+
+// One step from plan index r: three sweep slots, each flipping the buffers.
+cudaError_t launch_step(shasta_batch* b, int r) {
+  for (int s = 0; s < 3; ++s) {
+    for (const LaunchRec& L : b->plan[r][s]) {
+      cudaError_t e = launch_rec(b, L, b->cur, b->tune_var[L.axis]);
+      if (e != cudaSuccess) return e;
+    }
+    b->cur ^= 1;
+  }
+  return cudaSuccess;
+}
+
+// Times (variant, segment length) per axis: every event sweeps along the
+// axis from the current buffer into the other one (the state is not
+// changed).  Segmenting and the variant do not change results.
+shasta_status autotune(shasta_batch* b) {
+  if (!b->nlive) return SHASTA_OK;
+  static const int lens[] = {0, 96, 48};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0), "cudaEventCreate");
+  CK(cudaEventCreate(&e1), "cudaEventCreate");
+  shasta_status st = SHASTA_OK;
+  const int n = slots_in_use(b);
+  for (int a = 0; a < 3 && st == SHASTA_OK; ++a) {
+    float best = 1e30f;
+    int bv = 0, bl = 0;
+    for (int len : lens) {
+      st = upload_desc(b, a, len);
+      if (st != SHASTA_OK) break;
+      std::vector<int> host;
+      std::vector<LaunchRec> recs;
+      for (int k = 0; k < 2; ++k) {
+        std::vector<int> ids;
+        for (int i = 0; i < n; ++i)
+          if (b->ev[i].live && b->ev[i].eos.kind == k) ids.push_back(i);
+        if (!ids.empty()) recs.push_back(make_list(b, ids, a, k, a, len, host));
+      }
+      st = upload_plan(b, host);
+      if (st != SHASTA_OK) break;
+      for (int var = 0; var < 2; ++var) {
+        cudaError_t ce = cudaSuccess;
+        for (const LaunchRec& L : recs)
+          if (ce == cudaSuccess) ce = launch_rec(b, L, b->cur, var);
+        if (ce == cudaSuccess) ce = cudaEventRecord(e0, b->stream);
+        for (int rep = 0; rep < 3 && ce == cudaSuccess; ++rep)
+          for (const LaunchRec& L : recs)
+            if (ce == cudaSuccess) ce = launch_rec(b, L, b->cur, var);
+        if (ce == cudaSuccess) ce = cudaEventRecord(e1, b->stream);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+        if (ce != cudaSuccess) {
+          st = cuda_fail(b, ce, "autotune");
+          break;
+        }
+        if (ms < best) {
+          best = ms;
+          bv = var;
+          bl = len;
+        }
+      }
+    }
+    b->tune_var[a] = bv;
+    b->tune_len[a] = bl;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->plan_valid = false;
+  if (st == SHASTA_OK) b->tuned = true;
+  return st;
+}
+
+shasta_status ensure_staging(shasta_batch* b, long long cells) {
+  if ((size_t)cells <= b->staging_cells) return SHASTA_OK;
+  CK(cudaStreamSynchronize(b->stream), "sync");
+  cudaFree(b->staging);
+  b->staging = nullptr;
+  b->staging_cells = 0;
+  CK(cudaMalloc((void**)&b->staging, 6 * (size_t)cells * sizeof(double)), "cudaMalloc staging");
+  b->staging_cells = (size_t)cells;
+  return SHASTA_OK;
+}
+
+Event* find(shasta_batch* b, int id) {
+  if (!b || id < 0 || id >= (int)b->ev.size() || !b->ev[id].live) return nullptr;
+  return &b->ev[id];
+}
+
+void release(shasta_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  drop_graph(b);
+  for (Event& e : b->ev) cudaFree(e.frozen);
+  cudaFree(b->pool);
+  cudaFree(b->d_desc);
+  cudaFreeHost(b->h_desc);
+  cudaFree(b->d_count);
+  cudaFree(b->d_plan);
+  cudaFreeHost(b->h_plan);
+  cudaFree(b->staging);
+  cudaFree(b->partials);
+  cudaFree(b->d_tot);
+  cudaFreeHost(b->h_small);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+void shasta_batch_default_opts(shasta_batch_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->precision = SHASTA_FP32;
+  o->eta = 0.125;
+  o->delta = 0.0;
+  o->stream = nullptr;
+  o->device = 0;
+  o->check_input = 1;
+  o->autotune = 1;
+  o->use_graphs = 1;
+  o->max_events = 1024;
+  o->capacity_cells = 0;
+}
+
+shasta_status shasta_batch_create(const shasta_batch_opts* o, shasta_batch** out) {
+  g_batch_create_error.clear();
+  if (!out) return fail(nullptr, SHASTA_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!o) return fail(nullptr, SHASTA_EINVAL, "options are required (capacity_cells)");
+  shasta_batch_opts opts = *o;
+  if (opts.precision != SHASTA_FP32 && opts.precision != SHASTA_MIXED)
+    return fail(nullptr, SHASTA_EINVAL, "a batch runs FP32 or MIXED");
+  if (!(opts.eta >= 0.0 && opts.eta <= 0.5)) return fail(nullptr, SHASTA_EINVAL, "need 0 <= eta <= 0.5");
+  if (!(opts.delta >= 0.0 && opts.delta < 0.5)) return fail(nullptr, SHASTA_EINVAL, "need 0 <= delta < 0.5");
+  if (opts.delta == 0.0) opts.delta = 1e-6;
+  if (opts.max_events < 1 || opts.max_events > 65536)
+    return fail(nullptr, SHASTA_EINVAL, "max_events must be in 1..65536");
+  if (opts.capacity_cells < 1 || opts.capacity_cells > (1LL << 31))
+    return fail(nullptr, SHASTA_EINVAL, "capacity_cells must be in 1..2^31");
+  int ndev = 0;
+  cudaError_t ce = cudaGetDeviceCount(&ndev);
+  if (ce != cudaSuccess || ndev < 1)
+    return fail(nullptr, SHASTA_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(ce));
+  if (opts.device < 0 || opts.device >= ndev) return fail(nullptr, SHASTA_EINVAL, "bad device ordinal");
+
+  shasta_batch* b = new (std::nothrow) shasta_batch();
+  if (!b) return fail(nullptr, SHASTA_ENOMEM, "host allocation failed");
+  b->device = opts.device;
+  DeviceGuard dg(b->device);
+  b->o = opts;
+  b->mixed = opts.precision == SHASTA_MIXED;
+  b->cap = (opts.capacity_cells + kAlign - 1) / kAlign * kAlign;
+  b->ev.resize(opts.max_events);
+  b->cells.reset(b->cap);
+  {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) == cudaSuccess && sms > 0)
+      b->sm_count = sms;
+  }
+  auto bail = [&](cudaError_t err, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(err);
+    release(b);
+    return fail(nullptr, err == cudaErrorMemoryAllocation ? SHASTA_ENOMEM : SHASTA_ECUDA, m);
+  };
+  const size_t qbytes = (size_t)b->cap * 16, rbytes = (size_t)b->cap * 4;
+  cudaError_t err = cudaMalloc(&b->pool, 2 * (qbytes + rbytes));
+  if (err != cudaSuccess) return bail(err, "cudaMalloc pool");
+  for (int k = 0; k < 2; ++k) {
+    b->quad[k] = (float*)((char*)b->pool + k * qbytes);
+    b->rf[k] = (float*)((char*)b->pool + 2 * qbytes + k * rbytes);
+  }
+  err = cudaMalloc((void**)&b->d_desc, (size_t)opts.max_events * sizeof(EvDesc));
+  if (err != cudaSuccess) return bail(err, "cudaMalloc descriptors");
+  err = cudaMallocHost((void**)&b->h_desc, (size_t)opts.max_events * sizeof(EvDesc));
+  if (err != cudaSuccess) return bail(err, "cudaMallocHost descriptors");
+  err = cudaMalloc((void**)&b->d_count, ((size_t)opts.max_events + 1) * sizeof(unsigned long long));
+  if (err != cudaSuccess) return bail(err, "cudaMalloc counters");
+  err = cudaMemset(b->d_count, 0, ((size_t)opts.max_events + 1) * sizeof(unsigned long long));
+  if (err != cudaSuccess) return bail(err, "cudaMemset counters");
+  err = cudaMalloc((void**)&b->partials, 5 * kTotBlocks * sizeof(double));
+  if (err != cudaSuccess) return bail(err, "cudaMalloc partials");
+  err = cudaMalloc((void**)&b->d_tot, 8 * sizeof(double));
+  if (err != cudaSuccess) return bail(err, "cudaMalloc totals");
+  err = cudaMallocHost((void**)&b->h_small, 16 * sizeof(double));
+  if (err != cudaSuccess) return bail(err, "cudaMallocHost");
+  err = b->mixed ? prepare_batch_mixed(b->occ) : prepare_batch_f32(b->occ);
+  if (err != cudaSuccess) return bail(err, "prepare batched kernels");
+  b->wpb = b->mixed ? sweep_warps_per_block_mixed() : sweep_warps_per_block_f32();
+  if (opts.stream) {
+    b->stream = (cudaStream_t)opts.stream;
+  } else {
+    err = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (err != cudaSuccess) return bail(err, "cudaStreamCreate");
+    b->own_stream = true;
+  }
+  *out = b;
+  return SHASTA_OK;
+}
+
+shasta_status shasta_batch_destroy(shasta_batch* b) {
+  if (!b) return SHASTA_OK;
+  DeviceGuard dg(b->device);
+  release(b);
+  return SHASTA_OK;
+}
+
+shasta_status shasta_batch_add(shasta_batch* b, const shasta_grid* g, double dx, double lambda,
+                               const shasta_eos* eos, const double* const fields[5], int kind,
+                               int mem, int* id) {
+  if (!b) return SHASTA_EINVAL;
+  if (!id) return fail(b, SHASTA_EINVAL, "id is NULL");
+  *id = -1;
+  if (!g) return fail(b, SHASTA_EINVAL, "grid is NULL");
+  if (g->nx < 1 || g->ny < 1 || g->nz < 1) return fail(b, SHASTA_EINVAL, "grid sizes must be >= 1");
+  if (g->bc < SHASTA_BC_REFLECT || g->bc > SHASTA_BC_FROZEN)
+    return fail(b, SHASTA_EINVAL, "unknown boundary rule");
+  if (!(dx > 0) || !isfinite(dx)) return fail(b, SHASTA_EINVAL, "dx must be > 0");
+  if (!(lambda > 0.0 && lambda <= 0.5)) return fail(b, SHASTA_EINVAL, "need 0 < lambda <= 0.5");
+  shasta_eos e{SHASTA_EOS_IDEAL, 0.0, 0.0};
+  if (eos) e = *eos;
+  if (e.kind != SHASTA_EOS_IDEAL && e.kind != SHASTA_EOS_BAG) return fail(b, SHASTA_EINVAL, "unknown EoS");
+  if (e.kind == SHASTA_EOS_BAG && !(e.B >= 0.0 && 4.0 * e.B <= e.e_c))
+    return fail(b, SHASTA_EINVAL, "bag EoS needs 0 <= 4B <= e_c");
+  if (!fields) return fail(b, SHASTA_EINVAL, "fields is NULL");
+  for (int k = 0; k < 5; ++k)
+    if (!fields[k]) return fail(b, SHASTA_EINVAL, "NULL field pointer");
+  if (kind != SHASTA_STATE_CONSERVED && kind != SHASTA_STATE_PRIMITIVE)
+    return fail(b, SHASTA_EINVAL, "bad state kind");
+  if (mem != SHASTA_MEM_HOST && mem != SHASTA_MEM_DEVICE) return fail(b, SHASTA_EINVAL, "bad mem");
+  const long long ncell = (long long)g->nx * g->ny * g->nz;
+  if (ncell > b->cap) return fail(b, SHASTA_EINVAL, "grid larger than the pool");
+  int slot = -1;
+  for (int i = 0; i < (int)b->ev.size(); ++i)
+    if (!b->ev[i].live) {
+      slot = i;
+      break;
+    }
+  if (slot < 0) return fail(b, SHASTA_EAGAIN, "no free event slot");
+  DeviceGuard dg(b->device);
+  const long long off = b->cells.alloc(ncell);
+  if (off < 0) return fail(b, SHASTA_EAGAIN, "no contiguous room for the grid in the pool");
+  Event ev;
+  ev.g = *g;
+  ev.lambda = lambda;
+  ev.eos = e;
+  ev.off = off;
+  ev.ncell = ncell;
+  auto undo = [&](shasta_status s) {
+    cudaFree(ev.frozen);
+    b->cells.release(off, ncell);
+    return s;
+  };
+  if (g->bc == SHASTA_BC_FROZEN) {
+    cudaError_t ce = cudaMalloc(&ev.frozen, frozen_elems(g->nx, g->ny, g->nz) * sizeof(float));
+    if (ce != cudaSuccess) {
+      ev.frozen = nullptr;
+      return undo(cuda_fail(b, ce, "cudaMalloc frozen"));
+    }
+  }
+  const double* d[5];
+  if (mem == SHASTA_MEM_DEVICE) {
+    for (int k = 0; k < 5; ++k) d[k] = fields[k];
+  } else {
+    shasta_status s = ensure_staging(b, ncell);
+    if (s != SHASTA_OK) return undo(s);
+    for (int k = 0; k < 5; ++k) {
+      double* dd = b->staging + (size_t)k * ncell;
+      cudaError_t ce = cudaMemcpyAsync(dd, fields[k], ncell * sizeof(double), cudaMemcpyHostToDevice,
+                                       b->stream);
+      if (ce != cudaSuccess) return undo(cuda_fail(b, ce, "cudaMemcpyAsync H2D"));
+      d[k] = dd;
+    }
+  }
+  unsigned long long* scratch = b->d_count + b->o.max_events;
+  if (b->o.check_input) {
+    cudaError_t ce = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), b->stream);
+    if (ce == cudaSuccess)
+      ce = kind == SHASTA_STATE_PRIMITIVE ? launch_check_prims(d, ncell, scratch, b->stream)
+                                          : launch_check_cons(d, ncell, scratch, b->stream);
+    unsigned long long* h = reinterpret_cast<unsigned long long*>(b->h_small + 8);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(h, scratch, sizeof *h, cudaMemcpyDeviceToHost, b->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(b->stream);
+    if (ce != cudaSuccess) return undo(cuda_fail(b, ce, "input check"));
+    if (*h) {
+      char m[160];
+      snprintf(m, sizeof m, "%llu cells are not physical (non-finite, %s)", *h,
+               kind == SHASTA_STATE_PRIMITIVE ? "e < 0, n < 0 or |v| >= 1" : "E < 0 or |M| >= E");
+      return undo(fail(b, SHASTA_EUNPHYSICAL, m));
+    }
+  }
+  const FieldView v = view_of(b, ev, b->cur);
+  cudaError_t ce = cudaSuccess;
+  if (kind == SHASTA_STATE_PRIMITIVE) {
+    ce = launch_prim2cons(d, v, ncell, 1, eos_params(b, ev), b->stream);
+  } else {
+    for (int k = 0; k < 5 && ce == cudaSuccess; ++k)
+      ce = launch_from_f64(d[k], v.p[k], v.s[k], ncell, 1, b->stream);
+  }
+  if (ce == cudaSuccess && ev.frozen)
+    ce = launch_frozen_capture(v, ev.frozen, g->nx, g->ny, g->nz, 1, b->stream);
+  if (ce == cudaSuccess)
+    ce = cudaMemsetAsync(b->d_count + slot, 0, sizeof(unsigned long long), b->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(b->stream);
+  if (ce != cudaSuccess) return undo(cuda_fail(b, ce, "set state"));
+  ev.live = true;
+  b->ev[slot] = ev;
+  ++b->nlive;
+  b->used += ncell;
+  b->plan_valid = false;
+  b->tuned = false;
+  *id = slot;
+  return SHASTA_OK;
+}
+
+shasta_status shasta_batch_remove(shasta_batch* b, int id) {
+  Event* e = find(b, id);
+  if (!e) return b ? fail(b, SHASTA_ENOTFOUND, "unknown event id") : SHASTA_EINVAL;
+  DeviceGuard dg(b->device);
+  CK(cudaStreamSynchronize(b->stream), "sync");
+  cudaFree(e->frozen);
+  b->cells.release(e->off, e->ncell);
+  b->used -= e->ncell;
+  *e = Event();
+  --b->nlive;
+  b->plan_valid = false;
+  b->tuned = false;
+  return SHASTA_OK;
+}
+
+shasta_status shasta_batch_step(shasta_batch* b, int nsteps) {
+  if (!b) return SHASTA_EINVAL;
+  if (nsteps < 0) return fail(b, SHASTA_EINVAL, "nsteps < 0");
+  if (!nsteps || !b->nlive) return SHASTA_OK;
+  DeviceGuard dg(b->device);
+  if (!b->tuned) {
+    model_choice(b);
+    if (b->o.autotune) {
+      shasta_status st = autotune(b);
+      if (st != SHASTA_OK) return st;
+    }
+    b->tuned = true;
+    b->plan_valid = false;
+  }
+  if (!b->plan_valid) {
+    shasta_status st = build_plan(b);
+    if (st != SHASTA_OK) return st;
+  }
+  const int n = slots_in_use(b);
+  while (nsteps > 0) {
+    const int r = (int)((b->bsteps - b->plan_base) % 6);
+    int done = 1;
+    if (b->o.use_graphs && nsteps >= 6) {
+      // six steps bring every event's phase and the buffer back: one graph
+      if (!b->graph || b->graph_r != r || b->graph_cur != b->cur) {
+        drop_graph(b);
+        const int cur0 = b->cur;
+        cudaGraph_t gr = nullptr;
+        CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        cudaError_t ce = cudaSuccess;
+        for (int k = 0; k < 6 && ce == cudaSuccess; ++k) ce = launch_step(b, (r + k) % 6);
+        cudaError_t ce2 = cudaStreamEndCapture(b->stream, &gr);
+        b->cur = cur0;
+        if (ce != cudaSuccess || ce2 != cudaSuccess) {
+          if (gr) cudaGraphDestroy(gr);
+          return cuda_fail(b, ce != cudaSuccess ? ce : ce2, "capture six steps");
+        }
+        ce = cudaGraphInstantiate(&b->graph, gr, 0);
+        cudaGraphDestroy(gr);
+        if (ce != cudaSuccess) {
+          b->graph = nullptr;
+          return cuda_fail(b, ce, "cudaGraphInstantiate");
+        }
+        b->graph_r = r;
+        b->graph_cur = cur0;
+      }
+      CK(cudaGraphLaunch(b->graph, b->stream), "cudaGraphLaunch");
+      done = 6;  // 18 buffer flips: cur unchanged
+    } else {
+      CK(launch_step(b, r), "batched sweep launch");
+    }
+    b->bsteps += done;
+    for (int i = 0; i < n; ++i)
+      if (b->ev[i].live) b->ev[i].steps += done;
+    nsteps -= done;
+  }
+  return SHASTA_OK;
+}
+
+shasta_status shasta_batch_sync(shasta_batch* b) {
+  if (!b) return SHASTA_EINVAL;
+  DeviceGuard dg(b->device);
+  CK(cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
+  return SHASTA_OK;
+}
+
+shasta_status shasta_batch_autotune(shasta_batch* b) {
+  if (!b) return SHASTA_EINVAL;
+  DeviceGuard dg(b->device);
+  model_choice(b);
+  shasta_status st = autotune(b);
+  return st;
+}
+
+shasta_status shasta_batch_get_conserved(shasta_batch* b, int id, double* const out[5], int mem) {
+  Event* e = find(b, id);
+  if (!e) return b ? fail(b, SHASTA_ENOTFOUND, "unknown event id") : SHASTA_EINVAL;
+  if (!out) return fail(b, SHASTA_EINVAL, "out is NULL");
+  if (mem != SHASTA_MEM_HOST && mem != SHASTA_MEM_DEVICE) return fail(b, SHASTA_EINVAL, "bad mem");
+  DeviceGuard dg(b->device);
+  if (mem == SHASTA_MEM_HOST) {
+    shasta_status s = ensure_staging(b, e->ncell);
+    if (s != SHASTA_OK) return s;
+  }
+  const FieldView v = view_of(b, *e, b->cur);
+  for (int k = 0; k < 5; ++k) {
+    if (!out[k]) continue;
+    double* d = mem == SHASTA_MEM_DEVICE ? out[k] : b->staging + (size_t)k * e->ncell;
+    CK(launch_to_f64(v.p[k], v.s[k], d, e->ncell, 1, b->stream), "convert out");
+    if (mem == SHASTA_MEM_HOST)
+      CK(cudaMemcpyAsync(out[k], d, e->ncell * sizeof(double), cudaMemcpyDeviceToHost, b->stream),
+         "cudaMemcpyAsync D2H");
+  }
+  CK(cudaStreamSynchronize(b->stream), "sync");
+  return SHASTA_OK;
+}
+
+shasta_status shasta_batch_get_primitives(shasta_batch* b, int id, double* const out[6], int mem) {
+  Event* e = find(b, id);
+  if (!e) return b ? fail(b, SHASTA_ENOTFOUND, "unknown event id") : SHASTA_EINVAL;
+  if (!out) return fail(b, SHASTA_EINVAL, "out is NULL");
+  if (mem != SHASTA_MEM_HOST && mem != SHASTA_MEM_DEVICE) return fail(b, SHASTA_EINVAL, "bad mem");
+  DeviceGuard dg(b->device);
+  if (mem == SHASTA_MEM_HOST) {
+    shasta_status s = ensure_staging(b, e->ncell);
+    if (s != SHASTA_OK) return s;
+  }
+  double* d[6];
+  for (int k = 0; k < 6; ++k)
+    d[k] = !out[k] ? nullptr : (mem == SHASTA_MEM_DEVICE ? out[k] : b->staging + (size_t)k * e->ncell);
+  CK(launch_recover(view_of(b, *e, b->cur), d, e->ncell, 1, eos_params(b, *e), b->stream), "recover");
+  if (mem == SHASTA_MEM_HOST)
+    for (int k = 0; k < 6; ++k)
+      if (out[k])
+        CK(cudaMemcpyAsync(out[k], d[k], e->ncell * sizeof(double), cudaMemcpyDeviceToHost,
+                           b->stream),
+           "cudaMemcpyAsync D2H");
+  CK(cudaStreamSynchronize(b->stream), "sync");
+  return SHASTA_OK;
+}
+
+shasta_status shasta_batch_totals(shasta_batch* b, int id, double out[5]) {
+  Event* e = find(b, id);
+  if (!e) return b ? fail(b, SHASTA_ENOTFOUND, "unknown event id") : SHASTA_EINVAL;
+  if (!out) return fail(b, SHASTA_EINVAL, "out is NULL");
+  DeviceGuard dg(b->device);
+  CK(launch_totals(view_of(b, *e, b->cur), e->ncell, 1, b->partials, b->d_tot, b->stream), "totals");
+  CK(cudaMemcpyAsync(b->h_small, b->d_tot, 5 * sizeof(double), cudaMemcpyDeviceToHost, b->stream),
+     "memcpy totals");
+  CK(cudaStreamSynchronize(b->stream), "sync");
+  for (int k = 0; k < 5; ++k) out[k] = b->h_small[k];
+  return SHASTA_OK;
+}
+
+int64_t shasta_batch_steps_done(const shasta_batch* b, int id) {
+  if (!b || id < 0 || id >= (int)b->ev.size() || !b->ev[id].live) return -1;
+  return b->ev[id].steps;
+}
+
+shasta_status shasta_batch_counters(shasta_batch* b, int id, int64_t out[1]) {
+  Event* e = find(b, id);
+  if (!e) return b ? fail(b, SHASTA_ENOTFOUND, "unknown event id") : SHASTA_EINVAL;
+  if (!out) return fail(b, SHASTA_EINVAL, "out is NULL");
+  DeviceGuard dg(b->device);
+  unsigned long long* h = reinterpret_cast<unsigned long long*>(b->h_small + 9);
+  CK(cudaMemcpyAsync(h, b->d_count + id, sizeof *h, cudaMemcpyDeviceToHost, b->stream),
+     "memcpy counters");
+  CK(cudaStreamSynchronize(b->stream), "sync");
+  out[0] = (int64_t)*h;
+  return SHASTA_OK;
+}
+
+shasta_status shasta_batch_info(shasta_batch* b, int64_t out[6]) {
+  if (!b || !out) return SHASTA_EINVAL;
+  out[0] = b->nlive;
+  out[1] = b->used;
+  out[2] = b->cap;
+  out[3] = b->cells.largest();
+  int64_t launches = 0, items = 0;
+  if (b->plan_valid) {
+    const int r = (int)((b->bsteps - b->plan_base) % 6);
+    for (int s = 0; s < 3; ++s)
+      for (const LaunchRec& L : b->plan[r][s]) {
+        ++launches;
+        items += L.items;
+      }
+  }
+  out[4] = launches;
+  out[5] = items;
+  return SHASTA_OK;
+}
+
+void* shasta_batch_stream(const shasta_batch* b) { return b ? (void*)b->stream : nullptr; }
+
+const char* shasta_batch_last_error(const shasta_batch* b) {
+  return b ? b->err.c_str() : g_batch_create_error.c_str();
+}
+
+}  // extern "C"

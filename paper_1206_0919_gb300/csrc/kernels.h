@@ -21,6 +21,14 @@ cudaError_t prepare_sweep_f32(int occupancy[2][3][2]);
 cudaError_t prepare_sweep_mixed(int occupancy[2][3][2]);
 int sweep_warps_per_block_f32();
 int sweep_warps_per_block_mixed();
+// Batched FP32 / MIXED sweeps (one launch over the work list L, all along
+// `axis`); prepare_* as above for the batched kernels.
+cudaError_t prepare_batch_f32(int occupancy[2][3][2]);
+cudaError_t prepare_batch_mixed(int occupancy[2][3][2]);
+cudaError_t launch_batch_f32(const SweepParams& P, const BatchList& L, int axis, int eos,
+                             cudaStream_t s);
+cudaError_t launch_batch_mixed(const SweepParams& P, const BatchList& L, int axis, int eos,
+                               cudaStream_t s);
 
 // Where the five fields of a state live: element i of field k is at
 // p[k] + i * s[k] (in elements of the storage type).  FP64 states are five

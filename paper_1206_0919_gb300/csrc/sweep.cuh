@@ -70,6 +70,30 @@ struct SweepParams {
   float* rout;
 };
 
+// Batched sweeps: one event of a batch.  All events of a batch share the
+// batch's state arrays (qin/rin/qout/rout of SweepParams); the event's cells
+// are [off, off + nx*ny*nz) of each, x fastest.
+struct EvDesc {
+  long long off;
+  int nx, ny, nz, bc;
+  int nseg[3];                      // segments per line along each axis
+  int pad;
+  float tau_h, tau_f;               // lambda/2 and lambda
+  float htau_h, htau_f;             // half of each
+  float bag_B, bag_ec;
+  const float* frozen[3];           // frozen ghosts per axis (as SweepParams::frozen), or null
+  unsigned long long* clamp_count;  // the event's clamp counter
+};
+
+// Work list of one batched launch: list entry k is event idx[k], whose work
+// items (line group, segment) are numbered prefix[k] .. prefix[k+1]-1.
+struct BatchList {
+  const EvDesc* ev;
+  const int* idx;
+  const int* prefix;  // nlist + 1 entries
+  int nlist;
+};
+
 // ------------------------------------------------------------- recovery ----
 
 // Rest-frame e and p from E and the clamped |M| (Sec. 2: M = (E + p) v,

@@ -160,23 +160,119 @@ __device__ __forceinline__ void negate_par(f2& A, f2& B) {
   if (AXIS == 2) B ^= 0x8000000000000000ull;
 }
 
+// Geometry and coefficients of the event a work item belongs to, held in
+// registers (one event of a batch).
+struct ItemGeo {
+  long long off;     // first cell of the event in the state arrays
+  long long stride;  // cell stride along the line
+  long long plane;   // lines along this axis
+  long long sb, sc;  // first cell of line t = b + nb*c: off + b*sb + c*sc
+  int n, nb, bc, nseg;
+  const float* frozen;
+  float tau_h, tau_f, htau_h, htau_f, B, ec;
+  unsigned long long* clamp;
+};
+
+// Item geometry accessors.  GeoP reads the launch parameters at each use
+// (the single event of a launch: the values stay constant-bank operands);
+// GeoR returns the registers of an ItemGeo.
+struct GeoP {
+  const SweepParams& P;
+  __device__ __forceinline__ long long off() const { return 0; }
+  __device__ __forceinline__ long long stride() const { return P.stride; }
+  __device__ __forceinline__ long long plane() const { return P.plane; }
+  __device__ __forceinline__ long long sb() const { return P.sb; }
+  __device__ __forceinline__ long long sc() const { return P.sc; }
+  __device__ __forceinline__ int n() const { return P.n; }
+  __device__ __forceinline__ int nb() const { return P.nb; }
+  __device__ __forceinline__ int bc() const { return P.bc; }
+  __device__ __forceinline__ int nseg() const { return P.nseg; }
+  __device__ __forceinline__ const float* frozen() const { return static_cast<const float*>(P.frozen); }
+  __device__ __forceinline__ float tau_h() const { return float(P.tau_h); }
+  __device__ __forceinline__ float tau_f() const { return float(P.tau_f); }
+  __device__ __forceinline__ float htau_h() const { return float(P.htau_h); }
+  __device__ __forceinline__ float htau_f() const { return float(P.htau_f); }
+  __device__ __forceinline__ float B() const { return float(P.bag_B); }
+  __device__ __forceinline__ float ec() const { return float(P.bag_ec); }
+};
+struct GeoR {
+  ItemGeo g;
+  __device__ __forceinline__ long long off() const { return g.off; }
+  __device__ __forceinline__ long long stride() const { return g.stride; }
+  __device__ __forceinline__ long long plane() const { return g.plane; }
+  __device__ __forceinline__ long long sb() const { return g.sb; }
+  __device__ __forceinline__ long long sc() const { return g.sc; }
+  __device__ __forceinline__ int n() const { return g.n; }
+  __device__ __forceinline__ int nb() const { return g.nb; }
+  __device__ __forceinline__ int bc() const { return g.bc; }
+  __device__ __forceinline__ int nseg() const { return g.nseg; }
+  __device__ __forceinline__ const float* frozen() const { return g.frozen; }
+  __device__ __forceinline__ float tau_h() const { return g.tau_h; }
+  __device__ __forceinline__ float tau_f() const { return g.tau_f; }
+  __device__ __forceinline__ float htau_h() const { return g.htau_h; }
+  __device__ __forceinline__ float htau_f() const { return g.htau_f; }
+  __device__ __forceinline__ float B() const { return g.B; }
+  __device__ __forceinline__ float ec() const { return g.ec; }
+};
+
+template <int AXIS>
+__device__ __forceinline__ ItemGeo geo_of(const EvDesc& D) {
+  ItemGeo G;
+  const long long nx = D.nx, ny = D.ny, nz = D.nz;
+  G.off = D.off;
+  if (AXIS == 0) {
+    G.n = D.nx;
+    G.stride = 1;
+    G.plane = ny * nz;
+    G.nb = D.ny;
+    G.sb = nx;
+    G.sc = nx * ny;
+  } else if (AXIS == 1) {
+    G.n = D.ny;
+    G.stride = nx;
+    G.plane = nx * nz;
+    G.nb = D.nx;
+    G.sb = 1;
+    G.sc = nx * ny;
+  } else {
+    G.n = D.nz;
+    G.stride = nx * ny;
+    G.plane = nx * ny;
+    G.nb = D.nx;
+    G.sb = 1;
+    G.sc = nx;
+  }
+  G.bc = D.bc;
+  G.nseg = D.nseg[AXIS];
+  G.frozen = D.frozen[AXIS];
+  G.tau_h = D.tau_h;
+  G.tau_f = D.tau_f;
+  G.htau_h = D.htau_h;
+  G.htau_f = D.htau_f;
+  G.B = D.bag_B;
+  G.ec = D.bag_ec;
+  G.clamp = D.clamp_count;
+  return G;
+}
+
 // Copies extended position q of a line (first cell `cell0`, cell stride
 // `stride`) into a ring entry (quad at dq, R at dr).  Ghost positions follow
 // the boundary rule; frozen ghosts come from the frozen store (line t).
-__device__ __forceinline__ void copy_cell(const SweepParams& P, float* dq, float* dr,
-                                          long long cell0, long long stride, long long t, int q,
-                                          int n) {
-  if (P.bc == BC_FROZEN && (q < 0 || q >= n)) {
+template <class Geo>
+__device__ __forceinline__ void copy_cell(const SweepParams& P, const Geo& G, float* dq,
+                                          float* dr, long long cell0, long long stride,
+                                          long long t, int q, int n) {
+  if (G.bc() == BC_FROZEN && (q < 0 || q >= n)) {
     const int side = q < 0 ? 0 : 1;
     int layer = q < 0 ? -1 - q : q - n;
     layer = layer > NG - 1 ? NG - 1 : layer;
-    const float* fz = static_cast<const float*>(P.frozen) + (long long)(side * NG + layer) * NF * P.plane + t;
+    const float* fz = G.frozen() + (long long)(side * NG + layer) * NF * G.plane() + t;
 #pragma unroll
-    for (int f = 0; f < 4; ++f) cp_async4(dq + f, fz + f * P.plane);
-    cp_async4(dr, fz + 4 * P.plane);
+    for (int f = 0; f < 4; ++f) cp_async4(dq + f, fz + f * G.plane());
+    cp_async4(dr, fz + 4 * G.plane());
     return;
   }
-  const long long c = cell0 + (long long)map_pos(q, n, P.bc) * stride;
+  const long long c = cell0 + (long long)map_pos(q, n, G.bc()) * stride;
   cp_async16(dq, P.qin + 4 * c);
   cp_async4(dr, P.rin + c);
 }
@@ -442,36 +538,27 @@ using bc_ = std::integral_constant<bool, V>;
 //   half-step pass of (E, M) with newest cell q      -> U^h_{q-3}
 //   full-step pass of (E, M, R) with newest cell q-4 -> U^{n+1}_{q-7}
 
-template <int EOS, int AXIS, bool MIXED, int WARPS, int RING, int DIST, int MINB>
-__global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParams P) {
+// One work item: line group g, segment seg of the event described by G.
+template <int EOS, int AXIS, bool MIXED, int RING, int DIST, class Geo>
+__device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, long long local,
+                                           float* wsm, int lane, unsigned& nclamp) {
   constexpr bool XP = AXIS == 0;
   constexpr int LAG = 7;
   static_assert(RING == 8 && DIST == 3, "ring layout assumes 8 slots, 3 ahead");
-  extern __shared__ __align__(16) float smem[];
-
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  float* wsm = smem + (size_t)warp * Smem<AXIS, RING>::per_warp;
-  const int n = P.n;
-  const long long ngroups = (P.plane + LANES - 1) / LANES;
-  const long long nitems = ngroups * P.nseg;
-  const long long nwarps = (long long)gridDim.x * WARPS;
-  unsigned nclamp = 0;
-  // work items (line group g, segment seg), taken in a grid stride
-#pragma unroll 1
-  for (long long item = (long long)blockIdx.x * WARPS + warp; item < nitems; item += nwarps) {
-  const long long g = item % ngroups;
-  const int seg = (int)(item / ngroups);
+  const int n = G.n();
+  const long long ngroups = (G.plane() + LANES - 1) / LANES;
+  const long long g = local % ngroups;
+  const int seg = (int)(local / ngroups);
   const long long t = g * LANES + lane;
-  const bool valid = t < P.plane;
-  const long long tl = valid ? t : P.plane - 1;
-  const long long base = (tl % P.nb) * P.sb + (tl / P.nb) * P.sc;  // first cell of the line
+  const bool valid = t < G.plane();
+  const long long tl = valid ? t : G.plane() - 1;
+  const long long base = G.off() + (tl % G.nb()) * G.sb() + (tl / G.nb()) * G.sc();  // first cell of the line
   // segments split the line evenly (x path: on 8-cell chunk boundaries)
-  int s0 = (int)(((long long)seg * n) / P.nseg);
-  int s1 = (int)(((long long)(seg + 1) * n) / P.nseg);
+  int s0 = (int)(((long long)seg * n) / G.nseg());
+  int s1 = (int)(((long long)(seg + 1) * n) / G.nseg());
   if (XP) {
     s0 &= ~(CH - 1);
-    s1 = seg + 1 == P.nseg ? n : (s1 & ~(CH - 1));
+    s1 = seg + 1 == G.nseg() ? n : (s1 & ~(CH - 1));
   }
   // positions streamed: qs .. qe (the x path starts on a chunk boundary)
   const int qs = XP ? ((s0 - 2 * NG) & ~(CH - 1)) : s0 - 2 * NG;
@@ -486,14 +573,14 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParam
   i2 = i2 < trip ? i2 : trip;
   if (i2 < i1) i2 = i1;
 
-  const float tau_h = float(P.tau_h), tau_f = float(P.tau_f);
+  const float tau_h = G.tau_h(), tau_f = G.tau_f();
   const float eta = float(P.eta);
-  const float omd = float(P.omd), B = float(P.bag_B), ec = float(P.bag_ec);
-  const float htau_h = float(P.htau_h), htau_f = float(P.htau_f);
+  const float omd = float(P.omd), B = G.B(), ec = G.ec();
+  const float htau_h = G.htau_h(), htau_f = G.htau_f();
   const f2 omd2 = pk(omd, omd);
   const f2 eta2 = pk(eta, eta), m8c = pk(-0.125f, -0.125f);
   const f2 ht_h2 = pk(htau_h, htau_h), ht_f2 = pk(htau_f, htau_f);
-  const bool frozen = P.bc == BC_FROZEN;
+  const bool frozen = G.bc() == BC_FROZEN;
 
   auto x_slot = [&](int C) -> float* { return wsm + ((C + 3 * 4) % XSLOTS) * XSLOT; };
   // x path: cooperative copy of chunk C = positions [8C, 8C+8) of 32 rows
@@ -505,13 +592,13 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParam
     for (int k = 0; k < 8; ++k) {
       const int row = r0 + 4 * k;
       long long tr = g * LANES + row;
-      tr = tr < P.plane ? tr : P.plane - 1;
+      tr = tr < G.plane() ? tr : G.plane() - 1;
       float* dq = ring + row * XQSTR + pc * 4;
       float* dr = ring + XQ + row * XRSTR + pc;
       if (ghost) {
-        copy_cell(P, dq, dr, tr * P.sb, 1, tr, pos, n);
+        copy_cell(P, G, dq, dr, G.off() + tr * G.sb(), 1, tr, pos, n);
       } else {
-        const long long c = tr * P.sb + pos;
+        const long long c = G.off() + tr * G.sb() + pos;
         cp_async16(dq, P.qin + 4 * c);
         cp_async4(dr, P.rin + c);
       }
@@ -522,9 +609,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParam
     float* dq = slot + lane * 4;
     float* dr = slot + YQ + lane;
     if (ghost) {
-      copy_cell(P, dq, dr, base, P.stride, tl, q, n);
+      copy_cell(P, G, dq, dr, base, G.stride(), tl, q, n);
     } else {
-      const long long c = base + (long long)q * P.stride;
+      const long long c = base + (long long)q * G.stride();
       cp_async16(dq, P.qin + 4 * c);
       cp_async4(dr, P.rin + c);
     }
@@ -580,7 +667,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParam
     // ---- U^n_q (E, M)
     f2 uA, uB;
     rdq(sq, pq, uA, uB);
-    if (GH && flips(q, n, P.bc)) negate_par<AXIS>(uA, uB);
+    if (GH && flips(q, n, G.bc())) negate_par<AXIS>(uA, uB);
     if (!XP) {
       if (GH) {
         if (q + DIST <= qe) yz_issue(siss, q + DIST, true);
@@ -632,7 +719,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParam
       f2 vA, vB;
       rdq(sq4, pq4, vA, vB);
       const float vR = rdr(sq4, pq4);
-      if (GH && flips(q - 4, n, P.bc)) negate_par<AXIS>(vA, vB);
+      if (GH && flips(q - 4, n, G.bc())) negate_par<AXIS>(vA, vB);
       float a, nb, c;
       coeffs(tau_f, wh1, wh0, qpf, a, nb, c);
       f2 sA, sB;
@@ -656,7 +743,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParam
         sjo[XQ + lane * XRSTR + pj] = oR;
       }
     } else if (valid && jo >= s0 && jo < s1) {
-      const long long c = base + (long long)jo * P.stride;
+      const long long c = base + (long long)jo * G.stride();
       float o0, o1, o2, o3;
       up(oA, o0, o1);
       up(oB, o2, o3);
@@ -719,8 +806,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParam
           for (int k = 0; k < 8; ++k) {
             const int row = r0 + 4 * k;
             const long long tr = g * LANES + row;
-            if (tr < P.plane) {
-              const long long c = tr * P.sb + pos;
+            if (tr < G.plane()) {
+              const long long c = G.off() + tr * G.sb() + pos;
               *reinterpret_cast<float4*>(P.qout + 4 * c) =
                   *reinterpret_cast<const float4*>(ring + row * XQSTR + pc * 4);
               P.rout[c] = ring[XQ + row * XRSTR + pc];
@@ -734,8 +821,60 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParam
   }
   cp_wait<0>();
   __syncwarp();
-  }  // work items
-  if (nclamp && P.clamp_count) atomicAdd(P.clamp_count, (unsigned long long)nclamp);
+}
+
+// The work items of one launch, (line group, segment) of the single event
+// of P or of the events of the work list L (BATCH), taken by the warps in a
+// grid stride.
+template <int EOS, int AXIS, bool MIXED, int WARPS, int RING, int DIST, bool BATCH>
+__device__ __forceinline__ void sweep_items(const SweepParams& P, const BatchList& L) {
+  extern __shared__ __align__(16) float smem[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  float* wsm = smem + (size_t)warp * Smem<AXIS, RING>::per_warp;
+  const long long nwarps = (long long)gridDim.x * WARPS;
+  const long long first = (long long)blockIdx.x * WARPS + warp;
+  unsigned nclamp = 0;
+  if constexpr (BATCH) {
+    const long long nitems = L.nlist > 0 ? L.prefix[L.nlist] : 0;
+#pragma unroll 1
+    for (long long item = first; item < nitems; item += nwarps) {
+      // list entry of the item: the largest k with prefix[k] <= item
+      int lo = 0, hi = L.nlist - 1;
+#pragma unroll 1
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (L.prefix[mid] <= item)
+          lo = mid;
+        else
+          hi = mid - 1;
+      }
+      const GeoR G{geo_of<AXIS>(L.ev[L.idx[lo]])};
+      sweep_item<EOS, AXIS, MIXED, RING, DIST>(P, G, item - L.prefix[lo], wsm, lane, nclamp);
+      if (nclamp && G.g.clamp) atomicAdd(G.g.clamp, (unsigned long long)nclamp);
+      nclamp = 0;
+    }
+  } else {
+    const GeoP G{P};
+    const long long nitems = ((P.plane + LANES - 1) / LANES) * P.nseg;
+#pragma unroll 1
+    for (long long item = first; item < nitems; item += nwarps)
+      sweep_item<EOS, AXIS, MIXED, RING, DIST>(P, G, item, wsm, lane, nclamp);
+    if (nclamp && P.clamp_count) atomicAdd(P.clamp_count, (unsigned long long)nclamp);
+  }
+}
+
+// One event: the launch's items are those of P.
+template <int EOS, int AXIS, bool MIXED, int WARPS, int RING, int DIST, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParams P) {
+  sweep_items<EOS, AXIS, MIXED, WARPS, RING, DIST, false>(P, BatchList{});
+}
+
+// A batch: the items of every event of the work list L, all swept along
+// AXIS; P supplies the batch's state arrays, eta and 1 - delta.
+template <int EOS, int AXIS, bool MIXED, int WARPS, int RING, int DIST, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB) sweep_batch_kernel(SweepParams P, BatchList L) {
+  sweep_items<EOS, AXIS, MIXED, WARPS, RING, DIST, true>(P, L);
 }
 
 }  // namespace fast

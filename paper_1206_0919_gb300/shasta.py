@@ -49,6 +49,15 @@ class Opts(C.Structure):
                 ("autotune", C.c_int), ("use_graphs", C.c_int)]
 
 
+class BatchOpts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("eta", C.c_double), ("delta", C.c_double),
+                ("stream", C.c_void_p), ("device", C.c_int), ("check_input", C.c_int),
+                ("autotune", C.c_int), ("use_graphs", C.c_int), ("max_events", C.c_int),
+                ("capacity_cells", C.c_int64)]
+
+
+STATE_CONSERVED, STATE_PRIMITIVE = 0, 1
+
 _lock = threading.Lock()
 _lib = None
 
@@ -79,6 +88,24 @@ SIGNATURES = {
     "shasta_last_error": (C.c_char_p, [_vp]),
     "shasta_status_string": (C.c_char_p, [C.c_int]),
     "shasta_version": (C.c_char_p, []),
+    # include/shasta_batch.h
+    "shasta_batch_default_opts": (None, [C.POINTER(BatchOpts)]),
+    "shasta_batch_create": (C.c_int, [C.POINTER(BatchOpts), C.POINTER(_vp)]),
+    "shasta_batch_destroy": (C.c_int, [_vp]),
+    "shasta_batch_add": (C.c_int, [_vp, C.POINTER(Grid), C.c_double, C.c_double, C.POINTER(Eos),
+                                   C.POINTER(_vp), C.c_int, C.c_int, C.POINTER(C.c_int)]),
+    "shasta_batch_remove": (C.c_int, [_vp, C.c_int]),
+    "shasta_batch_step": (C.c_int, [_vp, C.c_int]),
+    "shasta_batch_sync": (C.c_int, [_vp]),
+    "shasta_batch_autotune": (C.c_int, [_vp]),
+    "shasta_batch_get_conserved": (C.c_int, [_vp, C.c_int, C.POINTER(_vp), C.c_int]),
+    "shasta_batch_get_primitives": (C.c_int, [_vp, C.c_int, C.POINTER(_vp), C.c_int]),
+    "shasta_batch_totals": (C.c_int, [_vp, C.c_int, _dp]),
+    "shasta_batch_steps_done": (C.c_int64, [_vp, C.c_int]),
+    "shasta_batch_counters": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int64)]),
+    "shasta_batch_info": (C.c_int, [_vp, C.POINTER(C.c_int64)]),
+    "shasta_batch_stream": (_vp, [_vp]),
+    "shasta_batch_last_error": (C.c_char_p, [_vp]),
 }
 
 
@@ -294,3 +321,127 @@ class Solver:
     @property
     def stream(self):
         return lib().shasta_stream(self._h)
+
+
+def _bcheck(status, b=None):
+    if status != OK:
+        raise ShastaError(status, lib().shasta_batch_last_error(b).decode())
+
+
+def _eos_struct(eos, bag_B, bag_ec):
+    kind = {"ideal": EOS_IDEAL, "bag": EOS_BAG}[eos] if isinstance(eos, str) else eos
+    return Eos(kind, bag_B, bag_ec)
+
+
+class Batch:
+    """Many events in one device pool, advanced together (include/shasta_batch.h)."""
+
+    def __init__(self, capacity_cells, precision="fp32", max_events=1024, eta=0.125, delta=0.0,
+                 stream=None, device=0, check_input=True, autotune=True, use_graphs=True):
+        L = lib()
+        o = BatchOpts()
+        L.shasta_batch_default_opts(C.byref(o))
+        o.precision = PRECISIONS[precision] if isinstance(precision, str) else precision
+        o.eta = eta
+        o.delta = delta
+        o.stream = stream
+        o.device = device
+        o.check_input = 1 if check_input else 0
+        o.autotune = 1 if autotune else 0
+        o.use_graphs = 1 if use_graphs else 0
+        o.max_events = max_events
+        o.capacity_cells = int(capacity_cells)
+        h = _vp()
+        _bcheck(L.shasta_batch_create(C.byref(o), C.byref(h)))
+        self._h = h
+        self.shapes = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().shasta_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _add(self, shape, arrays, kind, lam, dx, bc, eos, bag_B, bag_ec):
+        nx, ny, nz = shape
+        g = Grid(nx, ny, nz, BCS[bc] if isinstance(bc, str) else bc)
+        e = _eos_struct(eos, bag_B, bag_ec)
+        p, mem, keep = _ptrs(list(arrays))
+        arr = (_vp * 5)(*p)
+        out = C.c_int(-1)
+        _bcheck(lib().shasta_batch_add(self._h, C.byref(g), dx, lam, C.byref(e), arr, kind, mem,
+                                       C.byref(out)), self._h)
+        self.shapes[out.value] = (nz, ny, nx)
+        return out.value
+
+    def add_conserved(self, shape, U, lam=0.4, dx=1.0, bc="reflect", eos="ideal", bag_B=0.1,
+                      bag_ec=0.5):
+        return self._add(shape, U, STATE_CONSERVED, lam, dx, bc, eos, bag_B, bag_ec)
+
+    def add_primitives(self, shape, prims, lam=0.4, dx=1.0, bc="reflect", eos="ideal",
+                       bag_B=0.1, bag_ec=0.5):
+        return self._add(shape, prims, STATE_PRIMITIVE, lam, dx, bc, eos, bag_B, bag_ec)
+
+    def remove(self, eid):
+        _bcheck(lib().shasta_batch_remove(self._h, eid), self._h)
+        self.shapes.pop(eid, None)
+
+    def step(self, nsteps=1):
+        _bcheck(lib().shasta_batch_step(self._h, int(nsteps)), self._h)
+
+    def sync(self):
+        _bcheck(lib().shasta_batch_sync(self._h), self._h)
+
+    def autotune(self):
+        _bcheck(lib().shasta_batch_autotune(self._h), self._h)
+
+    def get_conserved(self, eid, out=None):
+        if out is None:
+            shape = self.shapes.get(eid)  # unknown ids reach the library (ENOTFOUND)
+            out = [None if shape is None else np.empty(shape) for _ in range(5)]
+        p, mem, keep = _ptrs(list(out))
+        _bcheck(lib().shasta_batch_get_conserved(self._h, eid, (_vp * 5)(*p), mem), self._h)
+        return out
+
+    def get_primitives(self, eid, out=None):
+        if out is None:
+            shape = self.shapes.get(eid)  # unknown ids reach the library (ENOTFOUND)
+            out = [None if shape is None else np.empty(shape) for _ in range(6)]
+        p, mem, keep = _ptrs(list(out))
+        _bcheck(lib().shasta_batch_get_primitives(self._h, eid, (_vp * 6)(*p), mem), self._h)
+        return dict(zip(("e", "vx", "vy", "vz", "n", "p"), out))
+
+    def totals(self, eid):
+        out = (C.c_double * 5)()
+        _bcheck(lib().shasta_batch_totals(self._h, eid, out), self._h)
+        return np.array(out[:])
+
+    def steps_done(self, eid):
+        return int(lib().shasta_batch_steps_done(self._h, eid))
+
+    def counters(self, eid):
+        out = (C.c_int64 * 1)()
+        _bcheck(lib().shasta_batch_counters(self._h, eid, out), self._h)
+        return int(out[0])
+
+    def info(self):
+        out = (C.c_int64 * 6)()
+        _bcheck(lib().shasta_batch_info(self._h, out), self._h)
+        keys = ("events", "cells_used", "capacity", "largest_free", "launches_per_step",
+                "items_per_step")
+        return dict(zip(keys, (int(v) for v in out)))
+
+    @property
+    def stream(self):
+        return lib().shasta_batch_stream(self._h)
