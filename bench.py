@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--mode", choices=["full", "kernels"], default="full",
                     help="kernels: only warmup + K steps (for profiler captures)")
+    ap.add_argument("--workload", choices=["single", "batch64"], default="single",
+                    help="single: one 200^3 hot-spot event (the headline); batch64: 64 events "
+                         "of sizes from {48,64,96,128,160}^3 advanced as one batch")
+    ap.add_argument("--events", type=int, default=64, help="batch64: number of events")
     return ap.parse_args()
 
 
@@ -91,7 +95,8 @@ def measured_peak():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("sweep.cuh", "sweep_f32.cu", "sweep_mixed.cu", "sweep_f64.cu"):
+    for f in ("sweep.cuh", "sweep_fast.cuh", "sweep_launch.cuh", "sweep_f32.cu",
+              "sweep_mixed.cu", "sweep_f64.cu"):
         with open(os.path.join(ROOT, "paper_1206_0919_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -411,12 +416,149 @@ def run_kernels_only(args):
     return 0
 
 
+# ------------------------------------------------------------- batched ----
+
+def batch_config(args, precision):
+    return {
+        "workload": f"batch_{args.events}_events",
+        "events": args.events,
+        "sizes": "N uniform in {48,64,96,128,160}, grids N^3",
+        "hot_spots": "5-40 per event (sigma 3-8 cells, amplitudes log-uniform in [0.1, 10])",
+        "radial_flow": "v_r = 0.1 r / R_box",
+        "precision": precision,
+        "eos": "ideal p=e/3", "bc": "reflect", "lambda": 0.4, "eta": 0.125, "seed": 3,
+        "event_steps": 100,
+        "l2": "working set of the batch (2 buffers x 5 fields) far above the 129 MB L2; no flush",
+        "data": "synthetic",
+    }
+
+
+def run_batch(args):
+    """64 uneven events (hot spots + radial flow) advanced as one batch: one
+    launch per (sweep slot, axis) over the work list of all events."""
+    import numpy as np
+    import torch
+
+    from paper_1206_0919_gb300 import shasta as S
+    from paper_1206_0919_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device (no CPU fallback exists)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    precision = args.precision if args.precision != "fp64" else "mixed"
+    evs = W.batch_events(n_events=args.events, seed=3 + 1000 * rank)
+    cells = [ev["N"] ** 3 for ev in evs]
+    total = sum(cells)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    host = [[pin(a) for a in W.event_prims(ev).as_list()] for ev in evs]
+    stream = torch.cuda.Stream()
+    cap = total + 64 * len(evs)
+    b = S.Batch(cap, precision=precision, max_events=len(evs), stream=stream.cuda_stream,
+                device=local)
+    ids = [b.add_primitives((ev["N"],) * 3, h) for ev, h in zip(evs, host)]
+    b.step(args.warmup)  # includes the autotuner's timing
+    b.sync()
+    info = b.info()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    ev0.record(stream)
+    b.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t_wall1 = time.time()
+    sampler.stop()
+    clocks = sampler.summary(t_wall0, t_wall1)
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * total * args.steps / (ms / 1e3)
+    launches_per_step = info["launches_per_step"]
+    bytes_per_step = total * 5 * 4 * 2 * 3
+    achieved = bytes_per_step / (ms / 1e3 / args.steps) / 1e9
+    peak, peak_kind = measured_peak()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                "kernel": f"sweep_batch_kernel ({precision}), all launches of a step",
+                "algorithmic_bytes_per_step": bytes_per_step}
+
+    # end to end through the public API: every event added from pinned host
+    # arrays, 100 steps, primitives of every event read back to pinned host
+    outs = [[torch.empty((ev["N"],) * 3, dtype=torch.float64).pin_memory().numpy()
+             for _ in range(6)] for ev in evs]
+    for i in ids:
+        b.remove(i)
+    t0 = time.perf_counter()
+    ids = [b.add_primitives((ev["N"],) * 3, h) for ev, h in zip(evs, host)]
+    b.step(100)
+    for i, o in zip(ids, outs):
+        b.get_primitives(i, o)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * total * 100 / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": 5 * 8 * total, "d2h_bytes_per_step": 6 * 8 * total,
+           "step": "all events: add from pinned host (includes the autotuner), 100 steps, "
+                   "primitives to pinned host"}
+    b.close()
+
+    # the same events one context at a time (each with its own launches)
+    t_single = 0.0
+    k1 = max(6, min(args.steps, 12))
+    for ev, h in zip(evs, host):
+        with S.Solver((ev["N"],) * 3, precision=precision, stream=stream.cuda_stream,
+                      device=local) as s1:
+            s1.set_primitives(*h)
+            s1.step(6)
+            s1.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s1.step(k1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_single += e0.elapsed_time(e1) / 1e3 / k1
+    single_rate = total / t_single
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "mixed": "f32+f64"}[precision],
+            "data": "synthetic", "config": batch_config(args, precision),
+            "roofline": roofline, "cpu_baseline": None, "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+            "batch": {"cells": total, "launches_per_step": launches_per_step,
+                      "items_per_step": info["items_per_step"]},
+            "one_context_per_event": {"value": single_rate, "unit": UNIT,
+                                      "batch_speedup": value / world / single_rate},
+        }
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.mode == "kernels":
         return run_kernels_only(args)
+    if args.workload == "batch64":
+        return run_batch(args)
     return run_ours(args)
 
 
