@@ -33,6 +33,7 @@ UNITS = [
     ("aux.cu", EXACT),
     ("noalloc.cu", EXACT),
     ("batch.cu", EXACT),
+    ("server.cu", EXACT),
     ("sweep_f64.cu", EXACT),
     ("sweep_f32.cu", FAST),
     ("sweep_mixed.cu", FAST),

@@ -14,6 +14,7 @@
 
 #include "../../include/shasta_batch.h"
 #include "kernels.h"
+#include "range_alloc.h"
 
 using namespace shasta;
 
@@ -27,52 +28,6 @@ const int kAxisTable[18] = {0, 1, 2, 0, 2, 1, 2, 0, 1, 2, 1, 0, 1, 2, 0, 1, 0, 2
 
 constexpr long long kAlign = 32;  // cells: every event starts on a 512-byte quad boundary
 constexpr int kTotBlocks = 1024;  // partial sums of the totals reduction
-
-// First-fit allocator of cell ranges [0, cap) with coalescing frees.
-class RangeAlloc {
- public:
-  void reset(long long cap) {
-    free_.clear();
-    if (cap > 0) free_[0] = cap;
-  }
-  // Start of a free range of len cells (aligned to kAlign), or -1.
-  long long alloc(long long len) {
-    len = (len + kAlign - 1) / kAlign * kAlign;
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second >= len) {
-        const long long start = it->first, rest = it->second - len;
-        free_.erase(it);
-        if (rest > 0) free_[start + len] = rest;
-        return start;
-      }
-    }
-    return -1;
-  }
-  void release(long long start, long long len) {
-    len = (len + kAlign - 1) / kAlign * kAlign;
-    auto nx = free_.lower_bound(start);
-    if (nx != free_.end() && start + len == nx->first) {
-      len += nx->second;
-      nx = free_.erase(nx);
-    }
-    if (nx != free_.begin()) {
-      auto pv = std::prev(nx);
-      if (pv->first + pv->second == start) {
-        pv->second += len;
-        return;
-      }
-    }
-    free_[start] = len;
-  }
-  long long largest() const {
-    long long m = 0;
-    for (auto& kv : free_) m = std::max(m, kv.second);
-    return m;
-  }
-
- private:
-  std::map<long long, long long> free_;
-};
 
 struct Event {
   bool live = false;
@@ -106,7 +61,7 @@ struct shasta_batch {
   float* quad[2] = {};
   float* rf[2] = {};
   int cur = 0;
-  RangeAlloc cells;
+  RangeAlloc cells{kAlign};
   std::vector<Event> ev;
   int nlive = 0;
   long long used = 0;

@@ -1,0 +1,571 @@
+// server.cu -- the C ABI of include/shasta_serve.h: a worker thread that
+// admits submitted events into one resident batch by device-memory
+// footprint, advances them together and hands finished results back.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/shasta_serve.h"
+#include "range_alloc.h"
+
+using shasta::RangeAlloc;
+
+namespace {
+
+thread_local std::string g_server_create_error;
+
+constexpr int kMaxStaged = 4;             // events copied in ahead of admission
+constexpr long long kPoolAlign = 32;      // cells, as the batch pool
+constexpr long long kStateBytes = 40;     // device bytes of state per cell (two buffers)
+
+enum JobState { J_WAIT, J_STAGED, J_RESIDENT, J_OUT, J_DONE, J_FAILED };
+
+struct Job {
+  uint64_t ticket = 0;
+  shasta_event ev{};
+  long long ncell = 0;
+  std::vector<double> in;  // the five input arrays, copied at submit
+  JobState st = J_WAIT;
+  shasta_status status = SHASTA_OK;
+  double t_submit = 0, t_admit = 0, t_done = 0;
+  int bid = -1;
+  long long in_off = -1, out_off = -1, out_bytes = 0;
+  cudaEvent_t in_ready = nullptr;
+  int64_t steps_left = 0, steps = 0, clamps = 0;
+};
+
+using JobP = std::shared_ptr<Job>;
+
+}  // namespace
+
+struct shasta_server {
+  shasta_server_opts o{};
+  shasta_batch* batch = nullptr;
+  cudaStream_t compute = nullptr, copy = nullptr;
+  void* staging = nullptr;            // input half, then output half
+  long long in_cap = 0, out_cap = 0;
+  char* in_base = nullptr;
+  char* out_base = nullptr;
+  RangeAlloc in_arena{256}, out_arena{256};
+  long long pool_cells = 0;
+  std::chrono::steady_clock::time_point t0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<JobP> queue;                      // waiting, first come first served
+  std::unordered_map<uint64_t, JobP> jobs;     // every ticket not yet polled
+  std::vector<JobP> staged, resident, out;     // owned by the worker
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  shasta_status fatal = SHASTA_OK;
+  long long n_submitted = 0, n_done = 0, n_failed = 0, peak_resident = 0, batch_steps = 0;
+  std::string err;
+  std::thread worker;
+};
+
+namespace {
+
+double now(const shasta_server* s) {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - s->t0).count();
+}
+
+shasta_status fail(shasta_server* s, shasta_status st, const std::string& msg) {
+  if (s) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->err = msg;
+  } else {
+    g_server_create_error = msg;
+  }
+  return st;
+}
+
+long long pool_need(long long ncell) { return (ncell + kPoolAlign - 1) / kPoolAlign * kPoolAlign; }
+
+int n_outputs(const shasta_event& ev) {
+  int k = 0;
+  for (int i = 0; i < 6; ++i) k += ev.out_prims[i] != nullptr;
+  for (int i = 0; i < 5; ++i) k += ev.out_cons[i] != nullptr;
+  return k;
+}
+
+// Marks a job finished (or failed) and wakes pollers; called by the worker.
+void finish(shasta_server* s, const JobP& j, shasta_status st) {
+  std::lock_guard<std::mutex> lk(s->mu);
+  j->status = st;
+  j->st = st == SHASTA_OK ? J_DONE : J_FAILED;
+  j->t_done = now(s);
+  if (st == SHASTA_OK)
+    ++s->n_done;
+  else
+    ++s->n_failed;
+  s->cv_done.notify_all();
+}
+
+// A device error stops the server: every unfinished job fails.
+void stop_all(shasta_server* s, const std::string& where) {
+  std::string msg = where + ": " + shasta_batch_last_error(s->batch);
+  std::vector<JobP> all;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->fatal = SHASTA_ECUDA;
+    s->err = msg;
+    for (auto& kv : s->jobs)
+      if (kv.second->st != J_DONE && kv.second->st != J_FAILED) all.push_back(kv.second);
+    s->queue.clear();
+  }
+  for (auto& j : all) finish(s, j, SHASTA_ECUDA);
+}
+
+bool cuda_ok(shasta_server* s, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return true;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->fatal = SHASTA_ECUDA;
+  }
+  stop_all(s, std::string(where) + " (" + cudaGetErrorString(e) + ")");
+  return false;
+}
+
+// Copies the results of finished jobs from output staging into the callers'
+// buffers (the copies overlap the steps running on the compute stream).
+bool drain_out(shasta_server* s) {
+  for (const JobP& j : s->out) {
+    const double* base = (const double*)(s->out_base + j->out_off);
+    int k = 0;
+    const size_t bytes = (size_t)j->ncell * sizeof(double);
+    for (int i = 0; i < 6; ++i)
+      if (j->ev.out_prims[i]) {
+        if (!cuda_ok(s, cudaMemcpyAsync(j->ev.out_prims[i], base + (size_t)k * j->ncell, bytes,
+                                        cudaMemcpyDeviceToHost, s->copy),
+                     "copy out"))
+          return false;
+        ++k;
+      }
+    for (int i = 0; i < 5; ++i)
+      if (j->ev.out_cons[i]) {
+        if (!cuda_ok(s, cudaMemcpyAsync(j->ev.out_cons[i], base + (size_t)k * j->ncell, bytes,
+                                        cudaMemcpyDeviceToHost, s->copy),
+                     "copy out"))
+          return false;
+        ++k;
+      }
+    if (!cuda_ok(s, cudaStreamSynchronize(s->copy), "copy out")) return false;
+    s->out_arena.release(j->out_off, j->out_bytes);
+    finish(s, j, SHASTA_OK);
+  }
+  s->out.clear();
+  return true;
+}
+
+// Takes finished jobs out of the batch: results into output staging, from
+// where drain_out copies them to the callers (when the output staging is
+// full, pending copies are finished first: every job's outputs fit it).
+bool harvest(shasta_server* s) {
+  std::vector<JobP> keep;
+  for (const JobP& j : s->resident) {
+    if (j->steps_left > 0) {
+      keep.push_back(j);
+      continue;
+    }
+    int64_t c = 0;
+    shasta_status st = shasta_batch_counters(s->batch, j->bid, &c);
+    if (st != SHASTA_OK) return stop_all(s, "counters"), false;
+    j->clamps = c;
+    const int nout = n_outputs(j->ev);
+    j->out_bytes = (long long)nout * j->ncell * (long long)sizeof(double);
+    j->out_off = -1;
+    if (nout) {
+      j->out_off = s->out_arena.alloc(j->out_bytes);
+      if (j->out_off < 0) {
+        if (!drain_out(s)) return false;
+        j->out_off = s->out_arena.alloc(j->out_bytes);
+      }
+      if (j->out_off < 0) return stop_all(s, "output staging"), false;
+    }
+    double* pr[6] = {};
+    double* cs[5] = {};
+    int k = 0;
+    double* base = (double*)(s->out_base + (j->out_off > 0 ? j->out_off : 0));
+    bool any_p = false, any_c = false;
+    for (int i = 0; i < 6; ++i)
+      if (j->ev.out_prims[i]) {
+        pr[i] = base + (size_t)(k++) * j->ncell;
+        any_p = true;
+      }
+    for (int i = 0; i < 5; ++i)
+      if (j->ev.out_cons[i]) {
+        cs[i] = base + (size_t)(k++) * j->ncell;
+        any_c = true;
+      }
+    if (any_p && shasta_batch_get_primitives(s->batch, j->bid, pr, SHASTA_MEM_DEVICE) != SHASTA_OK)
+      return stop_all(s, "results"), false;
+    if (any_c && shasta_batch_get_conserved(s->batch, j->bid, cs, SHASTA_MEM_DEVICE) != SHASTA_OK)
+      return stop_all(s, "results"), false;
+    if (shasta_batch_remove(s->batch, j->bid) != SHASTA_OK) return stop_all(s, "remove"), false;
+    j->bid = -1;
+    if (j->out_off >= 0) {
+      std::lock_guard<std::mutex> lk(s->mu);
+      j->st = J_OUT;
+      s->out.push_back(j);
+    } else {
+      finish(s, j, SHASTA_OK);
+    }
+  }
+  s->resident.swap(keep);
+  return true;
+}
+
+// Admits staged jobs into the batch, in order, while the pool has room.
+bool admit(shasta_server* s) {
+  size_t i = 0;
+  for (; i < s->staged.size(); ++i) {
+    const JobP& j = s->staged[i];
+    if (!cuda_ok(s, cudaStreamWaitEvent(s->compute, j->in_ready, 0), "wait input")) return false;
+    const double* base = (const double*)(s->in_base + j->in_off);
+    const double* f[5];
+    for (int k = 0; k < 5; ++k) f[k] = base + (size_t)k * j->ncell;
+    int id = -1;
+    shasta_status st = shasta_batch_add(s->batch, &j->ev.grid, j->ev.dx, j->ev.lambda, &j->ev.eos,
+                                        f, j->ev.kind, SHASTA_MEM_DEVICE, &id);
+    if (st == SHASTA_EAGAIN) break;  // no contiguous room yet: retry next round
+    // the add has synchronised the compute stream: the staging is free
+    cudaEventDestroy(j->in_ready);
+    j->in_ready = nullptr;
+    s->in_arena.release(j->in_off, 5 * j->ncell * (long long)sizeof(double));
+    j->in_off = -1;
+    std::vector<double>().swap(j->in);
+    if (st == SHASTA_ECUDA || st == SHASTA_ENOMEM) return stop_all(s, "admit"), false;
+    if (st != SHASTA_OK) {
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->err = shasta_batch_last_error(s->batch);
+      }
+      finish(s, j, st);
+      continue;
+    }
+    j->bid = id;
+    j->steps_left = j->ev.nsteps;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      j->st = J_RESIDENT;
+      j->t_admit = now(s);
+      s->resident.push_back(j);
+      s->peak_resident = std::max<long long>(s->peak_resident, (long long)s->resident.size());
+    }
+  }
+  s->staged.erase(s->staged.begin(), s->staged.begin() + i);
+  return true;
+}
+
+void worker_main(shasta_server* s) {
+  cudaSetDevice(s->o.device);
+  for (;;) {
+    std::vector<JobP> to_stage;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      if (s->stop || s->fatal != SHASTA_OK) break;
+      if (s->queue.empty() && s->staged.empty() && s->resident.empty() && s->out.empty()) {
+        s->cv_work.wait_for(lk, std::chrono::milliseconds(20));
+        continue;
+      }
+      // first come first served: stage queue heads while slots, pool room
+      // (largest free run less what staged events will take) and staging
+      // memory allow
+      int64_t info[6] = {};
+      shasta_batch_info(s->batch, info);
+      long long room = info[3];
+      for (const JobP& j : s->staged) room -= pool_need(j->ncell);
+      int slots = s->o.max_resident - (int)s->resident.size() - (int)s->staged.size();
+      while (!s->queue.empty() && (int)(s->staged.size() + to_stage.size()) < kMaxStaged &&
+             slots > 0) {
+        const JobP& j = s->queue.front();
+        if (pool_need(j->ncell) > room) break;
+        const long long off = s->in_arena.alloc(5 * j->ncell * (long long)sizeof(double));
+        if (off < 0) break;
+        j->in_off = off;
+        j->st = J_STAGED;
+        room -= pool_need(j->ncell);
+        --slots;
+        to_stage.push_back(j);
+        s->queue.pop_front();
+      }
+    }
+    bool ok = true;
+    for (const JobP& j : to_stage) {
+      double* d = (double*)(s->in_base + j->in_off);
+      ok = cuda_ok(s, cudaEventCreateWithFlags(&j->in_ready, cudaEventDisableTiming), "event") &&
+           cuda_ok(s, cudaMemcpyAsync(d, j->in.data(), 5 * j->ncell * sizeof(double),
+                                      cudaMemcpyHostToDevice, s->copy),
+                   "copy in") &&
+           cuda_ok(s, cudaEventRecord(j->in_ready, s->copy), "event");
+      if (!ok) break;
+      s->staged.push_back(j);
+    }
+    if (!ok || !admit(s) || !harvest(s)) break;
+    if (!s->resident.empty()) {
+      int64_t k = s->o.steps_per_round;
+      for (const JobP& j : s->resident) k = std::min(k, j->steps_left);
+      if (shasta_batch_step(s->batch, (int)k) != SHASTA_OK) {
+        stop_all(s, "step");
+        break;
+      }
+      for (const JobP& j : s->resident) {
+        j->steps_left -= k;
+        j->steps += k;
+      }
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->batch_steps += k;
+    }
+    if (!drain_out(s)) break;  // overlaps the steps just enqueued
+    if (shasta_batch_sync(s->batch) != SHASTA_OK) {
+      stop_all(s, "sync");
+      break;
+    }
+  }
+}
+
+void release(shasta_server* s) {
+  if (!s) return;
+  if (s->worker.joinable()) {
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->stop = true;
+    }
+    s->cv_work.notify_all();
+    s->worker.join();
+  }
+  if (s->batch) shasta_batch_destroy(s->batch);
+  if (s->copy) cudaStreamSynchronize(s->copy);
+  for (const JobP& j : s->staged)
+    if (j->in_ready) cudaEventDestroy(j->in_ready);
+  cudaFree(s->staging);
+  if (s->compute) cudaStreamDestroy(s->compute);
+  if (s->copy) cudaStreamDestroy(s->copy);
+  delete s;
+}
+
+}  // namespace
+
+extern "C" {
+
+void shasta_server_default_opts(shasta_server_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->precision = SHASTA_FP32;
+  o->eta = 0.125;
+  o->delta = 0.0;
+  o->device = 0;
+  o->hbm_budget_bytes = 0;
+  o->staging_bytes = 0;
+  o->max_resident = 256;
+  o->max_queue = 4096;
+  o->steps_per_round = 2;
+}
+
+shasta_status shasta_server_create(const shasta_server_opts* o, shasta_server** out) {
+  g_server_create_error.clear();
+  if (!out) return fail(nullptr, SHASTA_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!o) return fail(nullptr, SHASTA_EINVAL, "options are required (hbm_budget_bytes)");
+  shasta_server_opts opts = *o;
+  if (opts.staging_bytes == 0) opts.staging_bytes = opts.hbm_budget_bytes / 8;
+  if (opts.hbm_budget_bytes <= 0 || opts.staging_bytes <= 0 ||
+      opts.staging_bytes >= opts.hbm_budget_bytes)
+    return fail(nullptr, SHASTA_EINVAL, "need 0 < staging_bytes < hbm_budget_bytes");
+  if (opts.max_resident < 1 || opts.max_resident > 65536)
+    return fail(nullptr, SHASTA_EINVAL, "max_resident must be in 1..65536");
+  if (opts.max_queue < 1) return fail(nullptr, SHASTA_EINVAL, "max_queue must be >= 1");
+  if (opts.steps_per_round < 1) return fail(nullptr, SHASTA_EINVAL, "steps_per_round must be >= 1");
+  const long long cells = (opts.hbm_budget_bytes - opts.staging_bytes) / kStateBytes;
+  if (cells < kPoolAlign) return fail(nullptr, SHASTA_EINVAL, "budget too small for any state");
+  int ndev = 0;
+  cudaError_t cd = cudaGetDeviceCount(&ndev);
+  if (cd != cudaSuccess || ndev < 1)
+    return fail(nullptr, SHASTA_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(cd));
+  if (opts.device < 0 || opts.device >= ndev) return fail(nullptr, SHASTA_EINVAL, "bad device ordinal");
+  shasta_server* s = new (std::nothrow) shasta_server();
+  if (!s) return fail(nullptr, SHASTA_ENOMEM, "host allocation failed");
+  s->o = opts;
+  s->t0 = std::chrono::steady_clock::now();
+  int prev = -1;
+  cudaGetDevice(&prev);
+  auto bail = [&](shasta_status st, const std::string& m) {
+    release(s);
+    if (prev >= 0) cudaSetDevice(prev);
+    return fail(nullptr, st, m);
+  };
+  cudaError_t ce = cudaSetDevice(opts.device);
+  if (ce != cudaSuccess) return bail(SHASTA_ECUDA, std::string("device: ") + cudaGetErrorString(ce));
+  ce = cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking);
+  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking);
+  if (ce != cudaSuccess) return bail(SHASTA_ECUDA, std::string("streams: ") + cudaGetErrorString(ce));
+  s->in_cap = s->out_cap = opts.staging_bytes / 512 * 256;
+  ce = cudaMalloc(&s->staging, s->in_cap + s->out_cap);
+  if (ce != cudaSuccess)
+    return bail(ce == cudaErrorMemoryAllocation ? SHASTA_ENOMEM : SHASTA_ECUDA,
+                std::string("staging: ") + cudaGetErrorString(ce));
+  s->in_base = (char*)s->staging;
+  s->out_base = (char*)s->staging + s->in_cap;
+  s->in_arena.reset(s->in_cap);
+  s->out_arena.reset(s->out_cap);
+  shasta_batch_opts bo;
+  shasta_batch_default_opts(&bo);
+  bo.precision = opts.precision;
+  bo.eta = opts.eta;
+  bo.delta = opts.delta;
+  bo.stream = s->compute;
+  bo.device = opts.device;
+  bo.check_input = 1;
+  bo.autotune = 0;  // the set of events changes every few steps: the model picks
+  bo.use_graphs = 1;
+  bo.max_events = opts.max_resident;
+  bo.capacity_cells = std::min<long long>(cells, 1LL << 31);
+  shasta_status st = shasta_batch_create(&bo, &s->batch);
+  if (st != SHASTA_OK) return bail(st, std::string("batch: ") + shasta_batch_last_error(nullptr));
+  s->pool_cells = bo.capacity_cells;
+  s->worker = std::thread(worker_main, s);
+  if (prev >= 0) cudaSetDevice(prev);
+  *out = s;
+  return SHASTA_OK;
+}
+
+shasta_status shasta_server_destroy(shasta_server* s) {
+  if (!s) return SHASTA_OK;
+  release(s);
+  return SHASTA_OK;
+}
+
+shasta_status shasta_submit(shasta_server* s, const shasta_event* ev, uint64_t* ticket) {
+  if (!s) return SHASTA_EINVAL;
+  if (!ev || !ticket) return fail(s, SHASTA_EINVAL, "event or ticket is NULL");
+  *ticket = 0;
+  const shasta_grid& g = ev->grid;
+  if (g.nx < 1 || g.ny < 1 || g.nz < 1) return fail(s, SHASTA_EINVAL, "grid sizes must be >= 1");
+  if (g.bc < SHASTA_BC_REFLECT || g.bc > SHASTA_BC_FROZEN)
+    return fail(s, SHASTA_EINVAL, "unknown boundary rule");
+  if (!(ev->dx > 0) || !isfinite(ev->dx)) return fail(s, SHASTA_EINVAL, "dx must be > 0");
+  if (!(ev->lambda > 0.0 && ev->lambda <= 0.5))
+    return fail(s, SHASTA_EINVAL, "need 0 < lambda <= 0.5");
+  if (ev->eos.kind != SHASTA_EOS_IDEAL && ev->eos.kind != SHASTA_EOS_BAG)
+    return fail(s, SHASTA_EINVAL, "unknown EoS");
+  if (ev->eos.kind == SHASTA_EOS_BAG && !(ev->eos.B >= 0.0 && 4.0 * ev->eos.B <= ev->eos.e_c))
+    return fail(s, SHASTA_EINVAL, "bag EoS needs 0 <= 4B <= e_c");
+  if (ev->kind != SHASTA_STATE_CONSERVED && ev->kind != SHASTA_STATE_PRIMITIVE)
+    return fail(s, SHASTA_EINVAL, "bad state kind");
+  if (ev->nsteps < 0) return fail(s, SHASTA_EINVAL, "nsteps < 0");
+  for (int k = 0; k < 5; ++k)
+    if (!ev->fields[k]) return fail(s, SHASTA_EINVAL, "NULL field pointer");
+  const long long ncell = (long long)g.nx * g.ny * g.nz;
+  if (pool_need(ncell) > s->pool_cells) return fail(s, SHASTA_EINVAL, "grid larger than the state pool");
+  if (5 * ncell * (long long)sizeof(double) > s->in_cap ||
+      n_outputs(*ev) * ncell * (long long)sizeof(double) > s->out_cap)
+    return fail(s, SHASTA_EINVAL, "grid larger than the staging memory");
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->fatal != SHASTA_OK) return SHASTA_ECUDA;
+    if ((int)s->queue.size() >= s->o.max_queue) {
+      s->err = "queue full";
+      return SHASTA_EAGAIN;
+    }
+  }
+  JobP j = std::make_shared<Job>();
+  j->ev = *ev;
+  for (int k = 0; k < 5; ++k) j->ev.fields[k] = nullptr;
+  j->ncell = ncell;
+  try {
+    j->in.resize(5 * (size_t)ncell);
+  } catch (const std::bad_alloc&) {
+    return fail(s, SHASTA_ENOMEM, "host copy of the input");
+  }
+  for (int k = 0; k < 5; ++k)
+    memcpy(j->in.data() + (size_t)k * ncell, ev->fields[k], ncell * sizeof(double));
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->fatal != SHASTA_OK) return SHASTA_ECUDA;
+    if ((int)s->queue.size() >= s->o.max_queue) {
+      s->err = "queue full";
+      return SHASTA_EAGAIN;
+    }
+    j->ticket = s->next_ticket++;
+    j->t_submit = now(s);
+    s->jobs[j->ticket] = j;
+    s->queue.push_back(j);
+    ++s->n_submitted;
+  }
+  s->cv_work.notify_one();
+  *ticket = j->ticket;
+  return SHASTA_OK;
+}
+
+shasta_status shasta_poll(shasta_server* s, uint64_t ticket, shasta_result* out) {
+  if (!s) return SHASTA_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(ticket);
+  if (it == s->jobs.end()) return SHASTA_ENOTFOUND;
+  const JobP& j = it->second;
+  if (j->st != J_DONE && j->st != J_FAILED) return SHASTA_EAGAIN;
+  if (out) {
+    out->t_submit = j->t_submit;
+    out->t_admit = j->t_admit;
+    out->t_done = j->t_done;
+    out->steps = j->steps;
+    out->clamp_count = j->clamps;
+  }
+  const shasta_status st = j->status;
+  s->jobs.erase(it);
+  return st;
+}
+
+shasta_status shasta_server_drain(shasta_server* s, double timeout_s) {
+  if (!s) return SHASTA_EINVAL;
+  std::unique_lock<std::mutex> lk(s->mu);
+  const auto until = std::chrono::steady_clock::now() +
+                     std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+                         std::chrono::duration<double>(timeout_s > 0 ? timeout_s : 0));
+  while (s->n_done + s->n_failed < s->n_submitted) {
+    if (s->cv_done.wait_until(lk, until) == std::cv_status::timeout &&
+        s->n_done + s->n_failed < s->n_submitted)
+      return SHASTA_ETIMEOUT;
+  }
+  return s->fatal != SHASTA_OK ? s->fatal : SHASTA_OK;
+}
+
+shasta_status shasta_server_stats(shasta_server* s, double out[8]) {
+  if (!s || !out) return SHASTA_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  out[0] = (double)s->n_submitted;
+  out[1] = (double)s->n_done;
+  out[2] = (double)s->n_failed;
+  out[3] = (double)s->queue.size();
+  out[4] = (double)(s->n_submitted - s->n_done - s->n_failed - (long long)s->queue.size());
+  out[5] = (double)s->peak_resident;
+  out[6] = (double)s->batch_steps;
+  out[7] = (double)s->pool_cells;
+  return SHASTA_OK;
+}
+
+double shasta_server_clock(const shasta_server* s) { return s ? now(s) : 0.0; }
+
+const char* shasta_server_last_error(const shasta_server* s) {
+  if (!s) return g_server_create_error.c_str();
+  // a copy per calling thread: the worker may set a new message meanwhile
+  thread_local std::string copy;
+  {
+    std::lock_guard<std::mutex> lk(const_cast<shasta_server*>(s)->mu);
+    copy = s->err;
+  }
+  return copy.c_str();
+}
+
+}  // extern "C"

@@ -58,6 +58,24 @@ class BatchOpts(C.Structure):
 
 STATE_CONSERVED, STATE_PRIMITIVE = 0, 1
 
+
+class ServerOpts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("eta", C.c_double), ("delta", C.c_double),
+                ("device", C.c_int), ("hbm_budget_bytes", C.c_int64),
+                ("staging_bytes", C.c_int64), ("max_resident", C.c_int),
+                ("max_queue", C.c_int), ("steps_per_round", C.c_int)]
+
+
+class Event(C.Structure):
+    _fields_ = [("grid", Grid), ("dx", C.c_double), ("lam", C.c_double), ("eos", Eos),
+                ("fields", C.c_void_p * 5), ("kind", C.c_int), ("nsteps", C.c_int),
+                ("out_prims", C.c_void_p * 6), ("out_cons", C.c_void_p * 5)]
+
+
+class Result(C.Structure):
+    _fields_ = [("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("steps", C.c_int64), ("clamp_count", C.c_int64)]
+
 _lock = threading.Lock()
 _lib = None
 
@@ -106,6 +124,16 @@ SIGNATURES = {
     "shasta_batch_info": (C.c_int, [_vp, C.POINTER(C.c_int64)]),
     "shasta_batch_stream": (_vp, [_vp]),
     "shasta_batch_last_error": (C.c_char_p, [_vp]),
+    # include/shasta_serve.h
+    "shasta_server_default_opts": (None, [C.POINTER(ServerOpts)]),
+    "shasta_server_create": (C.c_int, [C.POINTER(ServerOpts), C.POINTER(_vp)]),
+    "shasta_server_destroy": (C.c_int, [_vp]),
+    "shasta_submit": (C.c_int, [_vp, C.POINTER(Event), C.POINTER(C.c_uint64)]),
+    "shasta_poll": (C.c_int, [_vp, C.c_uint64, C.POINTER(Result)]),
+    "shasta_server_drain": (C.c_int, [_vp, C.c_double]),
+    "shasta_server_stats": (C.c_int, [_vp, C.POINTER(C.c_double)]),
+    "shasta_server_clock": (C.c_double, [_vp]),
+    "shasta_server_last_error": (C.c_char_p, [_vp]),
 }
 
 
@@ -445,3 +473,109 @@ class Batch:
     @property
     def stream(self):
         return lib().shasta_batch_stream(self._h)
+
+
+def _scheck(status, srv=None):
+    if status != OK:
+        raise ShastaError(status, lib().shasta_server_last_error(srv).decode())
+
+
+class Server:
+    """Serving loop (include/shasta_serve.h): submit events as they arrive,
+    poll for their results."""
+
+    def __init__(self, hbm_budget_bytes, precision="fp32", staging_bytes=0, max_resident=256,
+                 max_queue=4096, steps_per_round=2, eta=0.125, delta=0.0, device=0):
+        L = lib()
+        o = ServerOpts()
+        L.shasta_server_default_opts(C.byref(o))
+        o.precision = PRECISIONS[precision] if isinstance(precision, str) else precision
+        o.eta = eta
+        o.delta = delta
+        o.device = device
+        o.hbm_budget_bytes = int(hbm_budget_bytes)
+        o.staging_bytes = int(staging_bytes)
+        o.max_resident = max_resident
+        o.max_queue = max_queue
+        o.steps_per_round = steps_per_round
+        h = _vp()
+        _scheck(L.shasta_server_create(C.byref(o), C.byref(h)))
+        self._h = h
+        self._pending = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().shasta_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, shape, arrays, nsteps, kind="primitive", lam=0.4, dx=1.0, bc="reflect",
+               eos="ideal", bag_B=0.1, bag_ec=0.5, prims_out=True, cons_out=False):
+        """Queues one event (five host arrays, copied); returns its ticket.
+        Raises ShastaError with status EAGAIN when the queue is full."""
+        nx, ny, nz = shape
+        ev = Event()
+        ev.grid = Grid(nx, ny, nz, BCS[bc] if isinstance(bc, str) else bc)
+        ev.dx = dx
+        ev.lam = lam
+        ev.eos = _eos_struct(eos, bag_B, bag_ec)
+        keep = [np.ascontiguousarray(a, dtype=np.float64) for a in arrays]
+        for k in range(5):
+            assert keep[k].size == nx * ny * nz
+            ev.fields[k] = keep[k].ctypes.data
+        ev.kind = STATE_PRIMITIVE if kind == "primitive" else STATE_CONSERVED
+        ev.nsteps = int(nsteps)
+        outs = {"prims": [np.empty((nz, ny, nx)) for _ in range(6)] if prims_out else None,
+                "cons": [np.empty((nz, ny, nx)) for _ in range(5)] if cons_out else None}
+        if outs["prims"]:
+            for k in range(6):
+                ev.out_prims[k] = outs["prims"][k].ctypes.data
+        if outs["cons"]:
+            for k in range(5):
+                ev.out_cons[k] = outs["cons"][k].ctypes.data
+        t = C.c_uint64(0)
+        _scheck(lib().shasta_submit(self._h, C.byref(ev), C.byref(t)), self._h)
+        self._pending[t.value] = outs
+        return t.value
+
+    def poll(self, ticket):
+        """None while pending; a dict of timings and result arrays once the
+        event has finished; raises ShastaError if it failed."""
+        r = Result()
+        st = lib().shasta_poll(self._h, ticket, C.byref(r))
+        if st == EAGAIN:
+            return None
+        outs = self._pending.pop(ticket, None)
+        if st != OK:
+            raise ShastaError(st, lib().shasta_server_last_error(self._h).decode())
+        d = {"t_submit": r.t_submit, "t_admit": r.t_admit, "t_done": r.t_done,
+             "steps": int(r.steps), "clamp_count": int(r.clamp_count)}
+        if outs and outs["prims"]:
+            d["prims"] = dict(zip(("e", "vx", "vy", "vz", "n", "p"), outs["prims"]))
+        if outs and outs["cons"]:
+            d["cons"] = outs["cons"]
+        return d
+
+    def drain(self, timeout_s=60.0):
+        _scheck(lib().shasta_server_drain(self._h, float(timeout_s)), self._h)
+
+    def stats(self):
+        out = (C.c_double * 8)()
+        _scheck(lib().shasta_server_stats(self._h, out), self._h)
+        keys = ("submitted", "finished", "failed", "queued", "in_flight", "peak_resident",
+                "batch_steps", "pool_cells")
+        return dict(zip(keys, out[:]))
+
+    def clock(self):
+        return float(lib().shasta_server_clock(self._h))

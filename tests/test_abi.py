@@ -56,3 +56,25 @@ def test_create_without_gpu_fails_cleanly(lib):
     assert ei.value.status in (S.ECUDA, S.EINVAL)
     assert lib.shasta_status_string(S.EUNPHYSICAL) == b"SHASTA_EUNPHYSICAL"
     assert lib.shasta_version().startswith(b"shasta-gb300")
+
+
+def test_batch_and_server_without_gpu_fail_cleanly(lib):
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    with pytest.raises(S.ShastaError) as ei:
+        S.Batch(1 << 20)
+    assert ei.value.status == S.ECUDA
+    with pytest.raises(S.ShastaError) as ei:
+        S.Server(1 << 30)
+    assert ei.value.status == S.ECUDA
+    # option errors are reported before any device call
+    with pytest.raises(S.ShastaError) as ei:
+        S.Server(1 << 30, staging_bytes=1 << 31)
+    assert ei.value.status == S.EINVAL
+    with pytest.raises(S.ShastaError) as ei:
+        S.Batch(1 << 20, precision="fp64")
+    assert ei.value.status == S.EINVAL
