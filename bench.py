@@ -52,10 +52,17 @@ def parse():
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--mode", choices=["full", "kernels"], default="full",
                     help="kernels: only warmup + K steps (for profiler captures)")
-    ap.add_argument("--workload", choices=["single", "batch64"], default="single",
+    ap.add_argument("--workload", choices=["single", "batch64", "serve"], default="single",
                     help="single: one 200^3 hot-spot event (the headline); batch64: 64 events "
-                         "of sizes from {48,64,96,128,160}^3 advanced as one batch")
-    ap.add_argument("--events", type=int, default=64, help="batch64: number of events")
+                         "of sizes from {48,64,96,128,160}^3 advanced as one batch; serve: a "
+                         "Poisson stream of events through the serving loop")
+    ap.add_argument("--events", type=int, default=None,
+                    help="batch64: events in the batch (64); serve: events per rank (300)")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve: arrivals per second per rank")
+    ap.add_argument("--max-resident", type=int, default=64, help="serve: events resident at once")
+    ap.add_argument("--budget-gb", type=float, default=48.0, help="serve: device memory budget")
+    ap.add_argument("--steps-per-round", type=int, default=4,
+                    help="serve: steps enqueued between admission checks")
     return ap.parse_args()
 
 
@@ -451,6 +458,7 @@ def run_batch(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     precision = args.precision if args.precision != "fp64" else "mixed"
+    args.events = args.events or 64
     evs = W.batch_events(n_events=args.events, seed=3 + 1000 * rank)
     cells = [ev["N"] ** 3 for ev in evs]
     total = sum(cells)
@@ -464,6 +472,7 @@ def run_batch(args):
     b.step(args.warmup)  # includes the autotuner's timing
     b.sync()
     info = b.info()
+    launches0 = info["launches"]
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -482,6 +491,7 @@ def run_batch(args):
     sampler.stop()
     clocks = sampler.summary(t_wall0, t_wall1)
     ms = ev0.elapsed_time(ev1)
+    launches = b.info()["launches"] - launches0
     if dist is not None:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -539,11 +549,123 @@ def run_batch(args):
             "dtype": {"fp32": "f32", "mixed": "f32+f64"}[precision],
             "data": "synthetic", "config": batch_config(args, precision),
             "roofline": roofline, "cpu_baseline": None, "e2e": e2e,
-            "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+            "gpu_launches": launches, "clocks": clocks,
             "batch": {"cells": total, "launches_per_step": launches_per_step,
                       "items_per_step": info["items_per_step"]},
             "one_context_per_event": {"value": single_rate, "unit": UNIT,
                                       "batch_speedup": value / world / single_rate},
+        }
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+# ------------------------------------------------------------- serving ----
+
+def serve_config(args):
+    return {
+        "workload": f"serve_poisson_{args.rate:g}_per_s",
+        "events_per_rank": args.events, "rate_per_rank_hz": args.rate,
+        "sizes": "N in {64,96,128,192} with probabilities 0.4/0.3/0.2/0.1, grids N^3",
+        "eos": "alternating: ideal p=e/3 / bag (B=0.1, e_c=0.5)", "steps_per_event": 150,
+        "hot_spots": "as the single-event workload (20 spots per state)",
+        "inputs": "2 seeded states per (N, EoS), reused along the stream",
+        "precision": args.precision, "max_resident": args.max_resident,
+        "steps_per_round": args.steps_per_round,
+        "budget_gb": args.budget_gb, "bc": "reflect", "lambda": 0.4, "eta": 0.125,
+        "data": "synthetic",
+    }
+
+
+def run_serve(args):
+    """Poisson arrivals replayed in real time against the serving loop; each
+    rank runs its own server on its GPU with every world-th event."""
+    import numpy as np
+    import torch
+
+    from paper_1206_0919_gb300 import serving
+    from paper_1206_0919_gb300 import shasta as S
+    from paper_1206_0919_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device (no CPU fallback exists)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    precision = args.precision if args.precision != "fp64" else "fp32"
+    args.events = args.events or 300
+    stream = serving.shard(
+        W.serving_stream(n_events=args.events * world, rate_hz=args.rate * world, seed=4),
+        rank, world)
+    pool = {}
+    for N in W.SERVE_SIZES:
+        for eos in ("ideal", "bag"):
+            for v in range(2):
+                pr = W.hot_spots(N=N, seed=500 + 10 * N + 2 * v + (eos == "bag"), n_spots=20)
+                pool[(N, eos, v)] = [np.ascontiguousarray(a) for a in pr.as_list()]
+    inputs = lambda ev: pool[(ev["N"], ev["eos"], ev["seed"] % 2)]
+    budget = int(args.budget_gb * (1 << 30))
+    srv = S.Server(budget, precision=precision, staging_bytes=budget // 6,
+                   max_resident=args.max_resident, steps_per_round=args.steps_per_round,
+                   device=local)
+    # warm-up: a few small events through the whole loop
+    warm = [dict(t_arrival=0.0, N=64, eos=("ideal", "bag")[i % 2], steps=6, seed=i)
+            for i in range(max(1, args.warmup))]
+    serving.replay(srv, warm, inputs)
+    st0 = srv.stats()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    if dist is not None:
+        dist.barrier()
+    t_wall0 = time.time()
+    recs = serving.replay(srv, stream, inputs)
+    t_wall1 = time.time()
+    sampler.stop()
+    clocks = sampler.summary(t_wall0, t_wall1)
+    st1 = srv.stats()
+    srv.close()
+    span = max(r["t_done"] for r in recs) - min(r["t_arrival"] for r in recs)
+    lat_arr = [r["t_done"] - r["t_arrival"] for r in recs]
+    lat_sub = [r["t_done"] - r["t_submit"] for r in recs]
+    cells = sum(r["N"] ** 3 * r["steps"] for r in recs)
+    refusals = sum(r["refusals"] for r in recs)
+    if dist is not None:
+        t = torch.tensor([span], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        span = float(t.item())
+    lat_arr = serving.gather(lat_arr, dist)
+    lat_sub = serving.gather(lat_sub, dist)
+    n_all = len(lat_arr)
+    cells_all = serving.gather([cells], dist)
+    value = n_all / span
+    if rank == 0:
+        a, b = serving.summary(lat_arr), serving.summary(lat_sub)
+        out = {
+            "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
+            "steps": len(recs), "warmup": len(warm), "ms_per_step": span * 1e3 / max(1, len(recs)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "mixed": "f32+f64"}[precision], "data": "synthetic",
+            "config": serve_config(args),
+            "latency_s": {"p50": a["p50"], "p99": a["p99"], "mean": a["mean"], "max": a["max"],
+                          "from": "scheduled arrival to results in the caller's buffers"},
+            "latency_from_submit_s": {"p50": b["p50"], "p99": b["p99"]},
+            "served_cell_updates_per_s": sum(cells_all) / span,
+            "offered_events_per_s": args.rate * world,
+            "queue_full_refusals": refusals,
+            "peak_resident": st1["peak_resident"],
+            "worker_time_s": {k[2:]: round(st1[k] - st0[k], 4) for k in st1 if k.startswith("t_")},
+            "e2e": {"value": value, "unit": "events/s",
+                    "h2d_bytes_per_step": int(np.mean([40 * r["N"] ** 3 for r in recs])),
+                    "d2h_bytes_per_step": int(np.mean([48 * r["N"] ** 3 for r in recs])),
+                    "step": "one event (mean bytes): host arrays in, 150 steps, primitives "
+                            "to host buffers"},
+            "gpu_launches": int(st1["sweep_launches"] - st0["sweep_launches"]),
+            "clocks": clocks, "roofline": None, "cpu_baseline": None,
         }
         print(json.dumps(out), flush=True)
     if dist is not None:
@@ -559,6 +681,8 @@ def main():
         return run_kernels_only(args)
     if args.workload == "batch64":
         return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

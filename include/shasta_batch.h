@@ -107,8 +107,10 @@ shasta_status shasta_batch_counters(shasta_batch* b, int id, int64_t out[1]);
 
 /* out[0] resident events, out[1] cells in use, out[2] capacity in cells,
  * out[3] largest free run of cells, out[4] kernel launches per step of the
- * current work lists, out[5] work items per step. */
-shasta_status shasta_batch_info(shasta_batch* b, int64_t out[6]);
+ * current work lists, out[5] work items per step, out[6] sweep kernel
+ * launches issued since creation (those replayed in graphs included; the
+ * autotuner's trial launches not). */
+shasta_status shasta_batch_info(shasta_batch* b, int64_t out[7]);
 
 /* The batch's stream (cudaStream_t as void*). */
 void* shasta_batch_stream(const shasta_batch* b);

@@ -41,7 +41,7 @@ typedef struct shasta_server_opts {
   int64_t staging_bytes;    /* the staging part of the budget (half input, half output); 0: an eighth */
   int max_resident;         /* events advanced together at most (default 256) */
   int max_queue;            /* submitted events not yet resident at most (default 4096) */
-  int steps_per_round;      /* steps enqueued between admission checks (default 2) */
+  int steps_per_round;      /* steps enqueued between admission checks (default 4) */
 } shasta_server_opts;
 
 /* One event.  fields: five host arrays (E, Mx, My, Mz, R) or (e, vx, vy,
@@ -101,8 +101,10 @@ shasta_status shasta_server_drain(shasta_server* s, double timeout_s);
 /* out[0] submitted, out[1] finished, out[2] failed, out[3] waiting in the
  * queue, out[4] resident or being copied in/out, out[5] most events ever
  * resident at once, out[6] batched steps run, out[7] state pool capacity
- * in cells. */
-shasta_status shasta_server_stats(shasta_server* s, double out[8]);
+ * in cells, out[8] sweep kernel launches issued, out[9..15] seconds the
+ * worker spent copying inputs in, admitting, harvesting results, enqueueing
+ * steps, copying results out, waiting for the steps, and idle. */
+shasta_status shasta_server_stats(shasta_server* s, double out[16]);
 
 /* Seconds since the server was created (steady clock). */
 double shasta_server_clock(const shasta_server* s);

@@ -91,6 +91,14 @@ struct shasta_batch {
   std::vector<LaunchRec> plan[6][3];
   cudaGraphExec_t graph = nullptr;
   int graph_r = -1, graph_cur = -1;
+  int64_t graph_launches = 0;  // sweep launches in the graph
+  // side streams: the launches of one sweep slot run concurrently, so that
+  // the last wave of one overlaps the next (fork / join through events)
+  static constexpr int kSide = 5;
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kSide] = {};
+  int64_t launches = 0;        // sweep launches issued (graph replays included)
   std::string err;
 };
 
@@ -364,25 +372,41 @@ SweepParams batch_params(const shasta_batch* b, const LaunchRec& L, int from, in
   return P;
 }
 
-cudaError_t launch_rec(shasta_batch* b, const LaunchRec& L, int from, int variant) {
+cudaError_t launch_rec(shasta_batch* b, const LaunchRec& L, int from, int variant,
+                       cudaStream_t st = nullptr) {
   if (!L.nlist || !L.items) return cudaSuccess;
+  if (!st) st = b->stream;
+  ++b->launches;
   const SweepParams P = batch_params(b, L, from, variant);
   BatchList BL;
   BL.ev = b->d_desc;
   BL.idx = b->d_plan + L.idx_off;
   BL.prefix = b->d_plan + L.pre_off;
   BL.nlist = L.nlist;
-  return b->mixed ? launch_batch_mixed(P, BL, L.axis, L.eos, b->stream)
-                  : launch_batch_f32(P, BL, L.axis, L.eos, b->stream);
+  return b->mixed ? launch_batch_mixed(P, BL, L.axis, L.eos, st)
+                  : launch_batch_f32(P, BL, L.axis, L.eos, st);
 }
 
 // One step from plan index r: three sweep slots, each flipping the buffers.
 cudaError_t launch_step(shasta_batch* b, int r) {
   for (int s = 0; s < 3; ++s) {
-    for (const LaunchRec& L : b->plan[r][s]) {
-      cudaError_t e = launch_rec(b, L, b->cur, b->tune_var[L.axis]);
-      if (e != cudaSuccess) return e;
+    const std::vector<LaunchRec>& V = b->plan[r][s];
+    const int nside = std::min((int)V.size() - 1, shasta_batch::kSide);
+    cudaError_t e = cudaSuccess;
+    if (nside > 0) {
+      e = cudaEventRecord(b->fork, b->stream);
+      for (int i = 0; i < nside && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(b->side[i], b->fork, 0);
     }
+    for (size_t i = 0; i < V.size() && e == cudaSuccess; ++i) {
+      const int k = (int)i - 1;  // launch 0 on the batch stream, the others on side streams
+      cudaStream_t st = k >= 0 && k < nside ? b->side[k] : b->stream;
+      e = launch_rec(b, V[i], b->cur, b->tune_var[V[i].axis], st);
+    }
+    for (int i = 0; i < nside && e == cudaSuccess; ++i) {
+      e = cudaEventRecord(b->join[i], b->side[i]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join[i], 0);
+    }
+    if (e != cudaSuccess) return e;
     b->cur ^= 1;
   }
   return cudaSuccess;
@@ -479,6 +503,11 @@ void release(shasta_batch* b) {
   cudaFree(b->partials);
   cudaFree(b->d_tot);
   cudaFreeHost(b->h_small);
+  for (int i = 0; i < shasta_batch::kSide; ++i) {
+    if (b->side[i]) cudaStreamDestroy(b->side[i]);
+    if (b->join[i]) cudaEventDestroy(b->join[i]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
@@ -573,6 +602,13 @@ shasta_status shasta_batch_create(const shasta_batch_opts* o, shasta_batch** out
     if (err != cudaSuccess) return bail(err, "cudaStreamCreate");
     b->own_stream = true;
   }
+  for (int i = 0; i < shasta_batch::kSide; ++i) {
+    err = cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+    if (err != cudaSuccess) return bail(err, "side streams");
+  }
+  err = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (err != cudaSuccess) return bail(err, "fork event");
   *out = b;
   return SHASTA_OK;
 }
@@ -735,12 +771,15 @@ shasta_status shasta_batch_step(shasta_batch* b, int nsteps) {
       if (!b->graph || b->graph_r != r || b->graph_cur != b->cur) {
         drop_graph(b);
         const int cur0 = b->cur;
+        const int64_t l0 = b->launches;
         cudaGraph_t gr = nullptr;
         CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
         cudaError_t ce = cudaSuccess;
         for (int k = 0; k < 6 && ce == cudaSuccess; ++k) ce = launch_step(b, (r + k) % 6);
         cudaError_t ce2 = cudaStreamEndCapture(b->stream, &gr);
         b->cur = cur0;
+        b->graph_launches = b->launches - l0;
+        b->launches = l0;
         if (ce != cudaSuccess || ce2 != cudaSuccess) {
           if (gr) cudaGraphDestroy(gr);
           return cuda_fail(b, ce != cudaSuccess ? ce : ce2, "capture six steps");
@@ -755,6 +794,7 @@ shasta_status shasta_batch_step(shasta_batch* b, int nsteps) {
         b->graph_cur = cur0;
       }
       CK(cudaGraphLaunch(b->graph, b->stream), "cudaGraphLaunch");
+      b->launches += b->graph_launches;
       done = 6;  // 18 buffer flips: cur unchanged
     } else {
       CK(launch_step(b, r), "batched sweep launch");
@@ -860,7 +900,7 @@ shasta_status shasta_batch_counters(shasta_batch* b, int id, int64_t out[1]) {
   return SHASTA_OK;
 }
 
-shasta_status shasta_batch_info(shasta_batch* b, int64_t out[6]) {
+shasta_status shasta_batch_info(shasta_batch* b, int64_t out[7]) {
   if (!b || !out) return SHASTA_EINVAL;
   out[0] = b->nlive;
   out[1] = b->used;
@@ -877,6 +917,7 @@ shasta_status shasta_batch_info(shasta_batch* b, int64_t out[6]) {
   }
   out[4] = launches;
   out[5] = items;
+  out[6] = b->launches;
   return SHASTA_OK;
 }
 

@@ -53,7 +53,7 @@ using JobP = std::shared_ptr<Job>;
 struct shasta_server {
   shasta_server_opts o{};
   shasta_batch* batch = nullptr;
-  cudaStream_t compute = nullptr, copy = nullptr;
+  cudaStream_t compute = nullptr, copy = nullptr, copy_out = nullptr;
   void* staging = nullptr;            // input half, then output half
   long long in_cap = 0, out_cap = 0;
   char* in_base = nullptr;
@@ -61,17 +61,22 @@ struct shasta_server {
   RangeAlloc in_arena{256}, out_arena{256};
   long long pool_cells = 0;
   std::chrono::steady_clock::time_point t0;
-  std::mutex mu;
-  std::condition_variable cv_work, cv_done;
+  std::mutex mu;  // guards the queue, the job table, out_arena, deliver and the counters
+  std::condition_variable cv_work, cv_done, cv_deliver, cv_space;
   std::deque<JobP> queue;                      // waiting, first come first served
   std::unordered_map<uint64_t, JobP> jobs;     // every ticket not yet polled
-  std::vector<JobP> staged, resident, out;     // owned by the worker
+  std::vector<JobP> staged, resident;          // owned by the worker
+  std::deque<JobP> deliver;                    // results in output staging, for the deliverer
   uint64_t next_ticket = 1;
   bool stop = false;
   shasta_status fatal = SHASTA_OK;
   long long n_submitted = 0, n_done = 0, n_failed = 0, peak_resident = 0, batch_steps = 0;
+  long long sweep_launches = 0;
+  // worker time per phase (s): copy in, admit, harvest, step enqueue, copy
+  // out, waiting for the steps, idle
+  double t_phase[7] = {};
   std::string err;
-  std::thread worker;
+  std::thread worker, deliverer;
 };
 
 namespace {
@@ -113,8 +118,7 @@ void finish(shasta_server* s, const JobP& j, shasta_status st) {
 }
 
 // A device error stops the server: every unfinished job fails.
-void stop_all(shasta_server* s, const std::string& where) {
-  std::string msg = where + ": " + shasta_batch_last_error(s->batch);
+void stop_all(shasta_server* s, const std::string& msg) {
   std::vector<JobP> all;
   {
     std::lock_guard<std::mutex> lk(s->mu);
@@ -127,6 +131,11 @@ void stop_all(shasta_server* s, const std::string& where) {
   for (auto& j : all) finish(s, j, SHASTA_ECUDA);
 }
 
+// Message of a failed batch call (worker thread only: the batch is its own).
+std::string batch_msg(shasta_server* s, const char* where) {
+  return std::string(where) + ": " + shasta_batch_last_error(s->batch);
+}
+
 bool cuda_ok(shasta_server* s, cudaError_t e, const char* where) {
   if (e == cudaSuccess) return true;
   {
@@ -137,40 +146,49 @@ bool cuda_ok(shasta_server* s, cudaError_t e, const char* where) {
   return false;
 }
 
-// Copies the results of finished jobs from output staging into the callers'
-// buffers (the copies overlap the steps running on the compute stream).
-bool drain_out(shasta_server* s) {
-  for (const JobP& j : s->out) {
+// The deliverer thread: copies results from output staging into the
+// callers' buffers while the worker keeps the batch stepping.
+void deliverer_main(shasta_server* s) {
+  cudaSetDevice(s->o.device);
+  for (;;) {
+    JobP j;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      while (s->deliver.empty() && !s->stop) s->cv_deliver.wait_for(lk, std::chrono::milliseconds(20));
+      if (s->stop) return;
+      j = s->deliver.front();
+      s->deliver.pop_front();
+    }
+    const double t0 = now(s);
     const double* base = (const double*)(s->out_base + j->out_off);
-    int k = 0;
     const size_t bytes = (size_t)j->ncell * sizeof(double);
-    for (int i = 0; i < 6; ++i)
-      if (j->ev.out_prims[i]) {
-        if (!cuda_ok(s, cudaMemcpyAsync(j->ev.out_prims[i], base + (size_t)k * j->ncell, bytes,
-                                        cudaMemcpyDeviceToHost, s->copy),
-                     "copy out"))
-          return false;
-        ++k;
-      }
-    for (int i = 0; i < 5; ++i)
-      if (j->ev.out_cons[i]) {
-        if (!cuda_ok(s, cudaMemcpyAsync(j->ev.out_cons[i], base + (size_t)k * j->ncell, bytes,
-                                        cudaMemcpyDeviceToHost, s->copy),
-                     "copy out"))
-          return false;
-        ++k;
-      }
-    if (!cuda_ok(s, cudaStreamSynchronize(s->copy), "copy out")) return false;
-    s->out_arena.release(j->out_off, j->out_bytes);
+    int k = 0;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 6 && e == cudaSuccess; ++i)
+      if (j->ev.out_prims[i])
+        e = cudaMemcpyAsync(j->ev.out_prims[i], base + (size_t)(k++) * j->ncell, bytes,
+                            cudaMemcpyDeviceToHost, s->copy_out);
+    for (int i = 0; i < 5 && e == cudaSuccess; ++i)
+      if (j->ev.out_cons[i])
+        e = cudaMemcpyAsync(j->ev.out_cons[i], base + (size_t)(k++) * j->ncell, bytes,
+                            cudaMemcpyDeviceToHost, s->copy_out);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->copy_out);
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->out_arena.release(j->out_off, j->out_bytes);
+      s->t_phase[4] += now(s) - t0;
+      s->cv_space.notify_all();
+    }
+    if (e != cudaSuccess) {
+      cuda_ok(s, e, "copy out");
+      return;
+    }
     finish(s, j, SHASTA_OK);
   }
-  s->out.clear();
-  return true;
 }
 
 // Takes finished jobs out of the batch: results into output staging, from
-// where drain_out copies them to the callers (when the output staging is
-// full, pending copies are finished first: every job's outputs fit it).
+// where the deliverer copies them to the callers.
 bool harvest(shasta_server* s) {
   std::vector<JobP> keep;
   for (const JobP& j : s->resident) {
@@ -180,18 +198,19 @@ bool harvest(shasta_server* s) {
     }
     int64_t c = 0;
     shasta_status st = shasta_batch_counters(s->batch, j->bid, &c);
-    if (st != SHASTA_OK) return stop_all(s, "counters"), false;
+    if (st != SHASTA_OK) return stop_all(s, batch_msg(s, "counters")), false;
     j->clamps = c;
     const int nout = n_outputs(j->ev);
     j->out_bytes = (long long)nout * j->ncell * (long long)sizeof(double);
     j->out_off = -1;
     if (nout) {
-      j->out_off = s->out_arena.alloc(j->out_bytes);
-      if (j->out_off < 0) {
-        if (!drain_out(s)) return false;
-        j->out_off = s->out_arena.alloc(j->out_bytes);
+      // room in output staging: every job's outputs fit it, so waiting for
+      // the deliverer to free some always ends
+      std::unique_lock<std::mutex> lk(s->mu);
+      while ((j->out_off = s->out_arena.alloc(j->out_bytes)) < 0) {
+        if (s->stop || s->fatal != SHASTA_OK) return false;
+        s->cv_space.wait_for(lk, std::chrono::milliseconds(20));
       }
-      if (j->out_off < 0) return stop_all(s, "output staging"), false;
     }
     double* pr[6] = {};
     double* cs[5] = {};
@@ -209,15 +228,16 @@ bool harvest(shasta_server* s) {
         any_c = true;
       }
     if (any_p && shasta_batch_get_primitives(s->batch, j->bid, pr, SHASTA_MEM_DEVICE) != SHASTA_OK)
-      return stop_all(s, "results"), false;
+      return stop_all(s, batch_msg(s, "results")), false;
     if (any_c && shasta_batch_get_conserved(s->batch, j->bid, cs, SHASTA_MEM_DEVICE) != SHASTA_OK)
-      return stop_all(s, "results"), false;
-    if (shasta_batch_remove(s->batch, j->bid) != SHASTA_OK) return stop_all(s, "remove"), false;
+      return stop_all(s, batch_msg(s, "results")), false;
+    if (shasta_batch_remove(s->batch, j->bid) != SHASTA_OK) return stop_all(s, batch_msg(s, "remove")), false;
     j->bid = -1;
     if (j->out_off >= 0) {
       std::lock_guard<std::mutex> lk(s->mu);
       j->st = J_OUT;
-      s->out.push_back(j);
+      s->deliver.push_back(j);
+      s->cv_deliver.notify_one();
     } else {
       finish(s, j, SHASTA_OK);
     }
@@ -245,7 +265,7 @@ bool admit(shasta_server* s) {
     s->in_arena.release(j->in_off, 5 * j->ncell * (long long)sizeof(double));
     j->in_off = -1;
     std::vector<double>().swap(j->in);
-    if (st == SHASTA_ECUDA || st == SHASTA_ENOMEM) return stop_all(s, "admit"), false;
+    if (st == SHASTA_ECUDA || st == SHASTA_ENOMEM) return stop_all(s, batch_msg(s, "admit")), false;
     if (st != SHASTA_OK) {
       {
         std::lock_guard<std::mutex> lk(s->mu);
@@ -270,19 +290,30 @@ bool admit(shasta_server* s) {
 
 void worker_main(shasta_server* s) {
   cudaSetDevice(s->o.device);
+  double tp[7] = {};  // [4] (copy out) is kept by the deliverer
+  double mark = now(s);
+  auto lap = [&](int k) {
+    const double t = now(s);
+    tp[k] += t - mark;
+    mark = t;
+  };
   for (;;) {
     std::vector<JobP> to_stage;
     {
       std::unique_lock<std::mutex> lk(s->mu);
+      for (int k = 0; k < 7; ++k)
+        if (k != 4) s->t_phase[k] = tp[k];
       if (s->stop || s->fatal != SHASTA_OK) break;
-      if (s->queue.empty() && s->staged.empty() && s->resident.empty() && s->out.empty()) {
+      if (s->queue.empty() && s->staged.empty() && s->resident.empty()) {
         s->cv_work.wait_for(lk, std::chrono::milliseconds(20));
+        lk.unlock();
+        lap(6);
         continue;
       }
       // first come first served: stage queue heads while slots, pool room
       // (largest free run less what staged events will take) and staging
       // memory allow
-      int64_t info[6] = {};
+      int64_t info[7] = {};
       shasta_batch_info(s->batch, info);
       long long room = info[3];
       for (const JobP& j : s->staged) room -= pool_need(j->ncell);
@@ -312,46 +343,57 @@ void worker_main(shasta_server* s) {
       if (!ok) break;
       s->staged.push_back(j);
     }
-    if (!ok || !admit(s) || !harvest(s)) break;
+    lap(0);
+    if (!ok || !admit(s)) break;
+    lap(1);
+    if (!harvest(s)) break;
+    lap(2);
     if (!s->resident.empty()) {
       int64_t k = s->o.steps_per_round;
       for (const JobP& j : s->resident) k = std::min(k, j->steps_left);
       if (shasta_batch_step(s->batch, (int)k) != SHASTA_OK) {
-        stop_all(s, "step");
+        stop_all(s, batch_msg(s, "step"));
         break;
       }
       for (const JobP& j : s->resident) {
         j->steps_left -= k;
         j->steps += k;
       }
+      int64_t info[7] = {};
+      shasta_batch_info(s->batch, info);
       std::lock_guard<std::mutex> lk(s->mu);
       s->batch_steps += k;
+      s->sweep_launches = info[6];
     }
-    if (!drain_out(s)) break;  // overlaps the steps just enqueued
+    lap(3);
     if (shasta_batch_sync(s->batch) != SHASTA_OK) {
-      stop_all(s, "sync");
+      stop_all(s, batch_msg(s, "sync"));
       break;
     }
+    lap(5);
   }
 }
 
 void release(shasta_server* s) {
   if (!s) return;
-  if (s->worker.joinable()) {
-    {
-      std::lock_guard<std::mutex> lk(s->mu);
-      s->stop = true;
-    }
-    s->cv_work.notify_all();
-    s->worker.join();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
   }
+  s->cv_work.notify_all();
+  s->cv_deliver.notify_all();
+  s->cv_space.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  if (s->deliverer.joinable()) s->deliverer.join();
   if (s->batch) shasta_batch_destroy(s->batch);
   if (s->copy) cudaStreamSynchronize(s->copy);
+  if (s->copy_out) cudaStreamSynchronize(s->copy_out);
   for (const JobP& j : s->staged)
     if (j->in_ready) cudaEventDestroy(j->in_ready);
   cudaFree(s->staging);
   if (s->compute) cudaStreamDestroy(s->compute);
   if (s->copy) cudaStreamDestroy(s->copy);
+  if (s->copy_out) cudaStreamDestroy(s->copy_out);
   delete s;
 }
 
@@ -370,7 +412,7 @@ void shasta_server_default_opts(shasta_server_opts* o) {
   o->staging_bytes = 0;
   o->max_resident = 256;
   o->max_queue = 4096;
-  o->steps_per_round = 2;
+  o->steps_per_round = 4;
 }
 
 shasta_status shasta_server_create(const shasta_server_opts* o, shasta_server** out) {
@@ -409,6 +451,7 @@ shasta_status shasta_server_create(const shasta_server_opts* o, shasta_server** 
   if (ce != cudaSuccess) return bail(SHASTA_ECUDA, std::string("device: ") + cudaGetErrorString(ce));
   ce = cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking);
   if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking);
+  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&s->copy_out, cudaStreamNonBlocking);
   if (ce != cudaSuccess) return bail(SHASTA_ECUDA, std::string("streams: ") + cudaGetErrorString(ce));
   s->in_cap = s->out_cap = opts.staging_bytes / 512 * 256;
   ce = cudaMalloc(&s->staging, s->in_cap + s->out_cap);
@@ -435,6 +478,7 @@ shasta_status shasta_server_create(const shasta_server_opts* o, shasta_server** 
   if (st != SHASTA_OK) return bail(st, std::string("batch: ") + shasta_batch_last_error(nullptr));
   s->pool_cells = bo.capacity_cells;
   s->worker = std::thread(worker_main, s);
+  s->deliverer = std::thread(deliverer_main, s);
   if (prev >= 0) cudaSetDevice(prev);
   *out = s;
   return SHASTA_OK;
@@ -541,7 +585,7 @@ shasta_status shasta_server_drain(shasta_server* s, double timeout_s) {
   return s->fatal != SHASTA_OK ? s->fatal : SHASTA_OK;
 }
 
-shasta_status shasta_server_stats(shasta_server* s, double out[8]) {
+shasta_status shasta_server_stats(shasta_server* s, double out[16]) {
   if (!s || !out) return SHASTA_EINVAL;
   std::lock_guard<std::mutex> lk(s->mu);
   out[0] = (double)s->n_submitted;
@@ -552,6 +596,8 @@ shasta_status shasta_server_stats(shasta_server* s, double out[8]) {
   out[5] = (double)s->peak_resident;
   out[6] = (double)s->batch_steps;
   out[7] = (double)s->pool_cells;
+  out[8] = (double)s->sweep_launches;
+  for (int k = 0; k < 7; ++k) out[9 + k] = s->t_phase[k];
   return SHASTA_OK;
 }
 

@@ -464,10 +464,10 @@ class Batch:
         return int(out[0])
 
     def info(self):
-        out = (C.c_int64 * 6)()
+        out = (C.c_int64 * 7)()
         _bcheck(lib().shasta_batch_info(self._h, out), self._h)
         keys = ("events", "cells_used", "capacity", "largest_free", "launches_per_step",
-                "items_per_step")
+                "items_per_step", "launches")
         return dict(zip(keys, (int(v) for v in out)))
 
     @property
@@ -485,7 +485,7 @@ class Server:
     poll for their results."""
 
     def __init__(self, hbm_budget_bytes, precision="fp32", staging_bytes=0, max_resident=256,
-                 max_queue=4096, steps_per_round=2, eta=0.125, delta=0.0, device=0):
+                 max_queue=4096, steps_per_round=4, eta=0.125, delta=0.0, device=0):
         L = lib()
         o = ServerOpts()
         L.shasta_server_default_opts(C.byref(o))
@@ -571,10 +571,11 @@ class Server:
         _scheck(lib().shasta_server_drain(self._h, float(timeout_s)), self._h)
 
     def stats(self):
-        out = (C.c_double * 8)()
+        out = (C.c_double * 16)()
         _scheck(lib().shasta_server_stats(self._h, out), self._h)
         keys = ("submitted", "finished", "failed", "queued", "in_flight", "peak_resident",
-                "batch_steps", "pool_cells")
+                "batch_steps", "pool_cells", "sweep_launches", "t_copy_in", "t_admit",
+                "t_harvest", "t_step_enqueue", "t_copy_out", "t_wait_steps", "t_idle")
         return dict(zip(keys, out[:]))
 
     def clock(self):
