@@ -409,7 +409,8 @@ def run_kernels_only(args):
     from paper_1206_0919_gb300 import shasta as S
 
     N = args.grid
-    s = S.Solver((N, N, N), precision=args.precision)
+    # fixed launch choice (model), no graphs: every sweep is its own launch
+    s = S.Solver((N, N, N), precision=args.precision, autotune=False, use_graphs=False)
     s.set_primitives(*workload_prims(N).as_list())
     s.step(args.warmup)
     s.sync()

@@ -18,8 +18,11 @@
 //    from ring entries it no longer needs, so global accesses stay
 //    sector-complete.
 //  * Transport, differences and the antidiffusive flux run on the field
-//    pairs with the packed f32x2 add/sub/mul/fma of sm_100+; the flux
-//    limiter uses the three-input min.
+//    pairs (E, Mx), (My, Mz) as plain FP32 scalar operations; the flux
+//    limiter uses the three-input min.  (The packed f32x2 arithmetic of
+//    sm_100+ measured no faster here: the kernel is latency-bound at 12
+//    warps per SM, and forming register pairs cost one move for every two
+//    packed operations.)
 //  * The pass is written with differences (Delta, their first and second
 //    differences, Delta-hat) so that every carried quantity spans at most two
 //    positions: the loop is unrolled by 2 and all windows are renamed
@@ -32,9 +35,10 @@
 //    needs one division per pass.
 //  * The baryon density R is not transported at the half step: only E and M
 //    enter the recovery at n+1/2.
-//  * Recoveries at n (newest cell) and n+1/2 (four cells back) run together
-//    on packed pairs.  For p = e/3 with D = E^2 - |M|^2: s = sqrt(E^2 + 3D),
-//    p = D/(E + s), v = M/(E + p).  MIXED evaluates D in double-float
+//  * Recoveries at n (newest cell) and n+1/2 (four cells back) are two
+//    independent scalar chains.  For p = e/3 with D = E^2 - |M|^2:
+//    s = sqrt(E^2 + 3D), p = D/(E + s), v = M/(E + p).  The clamp counter
+//    is only touched on the rare clamped path.  MIXED evaluates D in double-float
 //    (error-free products and sums on the FP32 pipe), which removes the
 //    cancellation as v -> 1 at about FP64 accuracy of D.
 //  * The including units are built with -fmad=false: every fused
@@ -64,17 +68,17 @@ constexpr int XSLOT = XQ + LANES * XRSTR; // 1440 floats
 constexpr int YQ = 4 * LANES;
 constexpr int YSLOT = YQ + LANES;         // 160 floats
 
-// ------------------------------------------------------- packed f32x2 ----
+// ----------------------------------------------------------- field pairs ----
 
-typedef unsigned long long f2;  // two floats in one 64-bit register pair (lo, hi)
+// Two fields of a cell, (E, Mx) or (My, Mz), or one field of two cells.
+struct f2 {
+  float x, y;
+};
 
-__device__ __forceinline__ f2 pk(float lo, float hi) {
-  f2 r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
+__device__ __forceinline__ f2 pk(float lo, float hi) { return f2{lo, hi}; }
 __device__ __forceinline__ void up(f2 v, float& lo, float& hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+  lo = v.x;
+  hi = v.y;
 }
 __device__ __forceinline__ float lo_of(f2 v) {
   float a, b;
@@ -86,25 +90,11 @@ __device__ __forceinline__ float hi_of(f2 v) {
   up(v, a, b);
   return b;
 }
-__device__ __forceinline__ f2 add2(f2 a, f2 b) {
-  f2 r;
-  asm("add.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
-  f2 r;
-  asm("sub.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
-  f2 r;
-  asm("mul.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { return f2{a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) { return f2{a.x - b.x, a.y - b.y}; }
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return f2{a.x * b.x, a.y * b.y}; }
 __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
-  f2 r;
-  asm("fma.rn.ftz.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-  return r;
+  return f2{fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y)};
 }
 __device__ __forceinline__ float min3f(float a, float b, float c) {
   float r;
@@ -155,9 +145,9 @@ __device__ __forceinline__ bool flips(int q, int n, int bc) {
 // x -> hi of (E, Mx); y -> lo of (My, Mz); z -> hi of (My, Mz).
 template <int AXIS>
 __device__ __forceinline__ void negate_par(f2& A, f2& B) {
-  if (AXIS == 0) A ^= 0x8000000000000000ull;
-  if (AXIS == 1) B ^= 0x0000000080000000ull;
-  if (AXIS == 2) B ^= 0x8000000000000000ull;
+  if (AXIS == 0) A.y = -A.y;
+  if (AXIS == 1) B.x = -B.x;
+  if (AXIS == 2) B.y = -B.y;
 }
 
 // Geometry and coefficients of the event a work item belongs to, held in
@@ -346,45 +336,19 @@ __device__ __forceinline__ unsigned rec32(float E, float mx, float my, float mz,
   return clamped;
 }
 
-// Two independent recoveries at once (halves lo, hi): E, the three momenta
-// and the momentum along the sweep, packed.  Clamped or vacuum cells, the
-// bag EoS and MIXED take the scalar routine.  Returns the lo clamp flag.
+// The two recoveries of a streaming step (halves lo: U^n of the newest
+// cell, hi: U^(n+1/2) four cells back): E, the three momenta and the
+// momentum along the sweep.  cnt counts the lo cell when in_seg (a cell of
+// the item's own segment) and it was clamped or vacuum.
 template <int EOS, bool MIXED>
-__device__ __forceinline__ unsigned rec2(f2 E, f2 mx, f2 my, f2 mz, f2 mpar, f2 omd2, float omd,
-                                         float B, float ec, f2& w, f2& p) {
-  auto scalar = [&]() -> unsigned {
-    float El, Eh, xl, xh, yl, yh, zl, zh, al, ah, wl, wh_, pl, ph;
-    up(E, El, Eh);
-    up(mx, xl, xh);
-    up(my, yl, yh);
-    up(mz, zl, zh);
-    up(mpar, al, ah);
-    const unsigned c = rec32<EOS, MIXED>(El, xl, yl, zl, al, omd, B, ec, wl, pl);
-    rec32<EOS, MIXED>(Eh, xh, yh, zh, ah, omd, B, ec, wh_, ph);
-    w = pk(wl, wh_);
-    p = pk(pl, ph);
-    return c;
-  };
-  if (EOS == EOS_BAG || MIXED) return scalar();
-  const f2 M2 = fma2(mx, mx, fma2(my, my, mul2(mz, mz)));
-  const f2 E2 = mul2(E, E);
-  const f2 lim = mul2(omd2, E);
-  const f2 L2 = mul2(lim, lim);
-  float M2l, M2h, L2l, L2h, El, Eh;
-  up(M2, M2l, M2h);
-  up(L2, L2l, L2h);
-  up(E, El, Eh);
-  if (M2l > L2l || M2h > L2h || !(El > 0.0f) || !(Eh > 0.0f)) return scalar();
-  const f2 D = sub2(E2, M2);
-  float tl, th;
-  up(fma2(pk(3.0f, 3.0f), D, E2), tl, th);
-  float dl, dh;
-  up(add2(E, pk(sqrtf(tl), sqrtf(th))), dl, dh);
-  p = mul2(D, pk(__fdividef(1.0f, dl), __fdividef(1.0f, dh)));
-  float hl, hh;
-  up(add2(E, p), hl, hh);
-  w = mul2(mpar, pk(__fdividef(1.0f, hl), __fdividef(1.0f, hh)));
-  return 0u;
+__device__ __forceinline__ void rec2(f2 E, f2 mx, f2 my, f2 mz, f2 mpar, float omd, float B,
+                                     float ec, f2& w, f2& p, unsigned& cnt, bool in_seg) {
+  float wl, wh, pl, ph;
+  const unsigned c = rec32<EOS, MIXED>(E.x, mx.x, my.x, mz.x, mpar.x, omd, B, ec, wl, pl);
+  if (c) cnt += in_seg ? 1u : 0u;
+  rec32<EOS, MIXED>(E.y, mx.y, my.y, mz.y, mpar.y, omd, B, ec, wh, ph);
+  w = f2{wl, wh};
+  p = f2{pl, ph};
 }
 
 // ------------------------------------------------------- antidiffusion ----
@@ -429,12 +393,12 @@ __device__ __forceinline__ f2 step2(Line2& s, f2 u, f2 a2, f2 nb2, f2 c2, f2 src
   constexpr int P0 = K & 1, P1 = (K + 1) & 1;  // parity of k (= k-2, k-4) and of k-1 (= k-3)
   // values whose slots are overwritten below are consumed first
   const f2 aph = mul2(eta2, fma2(m8, s.D2[P1], s.Dh[P1]));        // A^ph_{k-3}
-  const f2 sg = (aph & 0x8000000080000000ull) | 0x3f8000003f800000ull;  // +-1
+  const f2 sg = f2{copysignf(1.0f, aph.x), copysignf(1.0f, aph.y)};  // +-1
   const f2 qm = mul2(sg, s.Dh[P0]);                              // s Dh_{k-4}
   const f2 t = add2(s.Uh[P1], s.A[P0]);                          // Uhat_{k-3} + A_{k-4}
   const f2 d = sub2(u, s.Up[P1]);                                // Delta_{k-1}
-  f2 uh = fma2(c2, s.Up[P1], fma2(a2, d, mul2(nb2, s.D[P0])));    // Uhat_{k-1}
-  if (SRC) uh = add2(uh, src);
+  // Uhat_{k-1}, the source folded into the innermost term
+  const f2 uh = fma2(c2, s.Up[P1], fma2(a2, d, SRC ? fma2(nb2, s.D[P0], src) : mul2(nb2, s.D[P0])));
   const f2 dd = sub2(d, s.D[P0]);                                // DD_{k-1}
   const f2 d2 = sub2(dd, s.DD[P0]);                              // D2_{k-2}
   const f2 dh = sub2(uh, s.Uh[P0]);                              // Dh_{k-2}
@@ -577,7 +541,6 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, l
   const float eta = float(P.eta);
   const float omd = float(P.omd), B = G.B(), ec = G.ec();
   const float htau_h = G.htau_h(), htau_f = G.htau_f();
-  const f2 omd2 = pk(omd, omd);
   const f2 eta2 = pk(eta, eta), m8c = pk(-0.125f, -0.125f);
   const f2 ht_h2 = pk(htau_h, htau_h), ht_f2 = pk(htau_f, htau_f);
   const bool frozen = G.bc() == BC_FROZEN;
@@ -686,8 +649,8 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, l
       const f2 mz = pk(hi_of(uB), hi_of(HB));
       const f2 mpar = AXIS == 0 ? mx : (AXIS == 1 ? my : mz);
       f2 w2, p2;
-      const unsigned c0 = rec2<EOS, MIXED>(E, mx, my, mz, mpar, omd2, omd, B, ec, w2, p2);
-      nclamp += ((unsigned)(q - s0) < (unsigned)(s1 - s0)) ? c0 : 0u;
+      rec2<EOS, MIXED>(E, mx, my, mz, mpar, omd, B, ec, w2, p2, nclamp,
+                       (unsigned)(q - s0) < (unsigned)(s1 - s0));
       float pl, phi, pwl, pwh;
       up(w2, wn0, wh0);
       up(p2, pl, phi);
