@@ -103,8 +103,8 @@ void shasta_default_opts(shasta_opts* o);
  * CFL number of Sec. 3 (0 < lambda <= 0.5); the time step is dt = lambda*dx.
  * eos may be NULL (ideal gas), o may be NULL (defaults).  Allocates two
  * copies of the five conserved fields on the device (double buffering,
- * Sec. 3.1.3).  Errors: EINVAL (sizes < 1, bad lambda/eta/eos, NULL out),
- * ENOMEM, ECUDA.  On error *out is NULL and shasta_last_error(NULL) holds
+ * Sec. 3.1.3).  Errors: EINVAL (sizes < 1, bad lambda/eta/eos, NULL out,
+ * FP32 / MIXED grids of 2^32 cells or more), ENOMEM, ECUDA.  On error *out is NULL and shasta_last_error(NULL) holds
  * the message. */
 shasta_status shasta_create(const shasta_grid* g, double dx, double lambda,
                             const shasta_eos* eos, const shasta_opts* o, shasta_ctx** out);

@@ -374,6 +374,8 @@ shasta_status shasta_create(const shasta_grid* g, double dx, double lambda, cons
     shasta_default_opts(&opts);
   if (opts.precision < SHASTA_FP64 || opts.precision > SHASTA_MIXED)
     return fail(nullptr, SHASTA_EINVAL, "unknown precision");
+  if (opts.precision != SHASTA_FP64 && (long long)g->nx * g->ny * g->nz >= (1LL << 32))
+    return fail(nullptr, SHASTA_EINVAL, "FP32 / MIXED grids hold fewer than 2^32 cells");
   if (!(opts.eta >= 0.0 && opts.eta <= 0.5)) return fail(nullptr, SHASTA_EINVAL, "need 0 <= eta <= 0.5");
   if (!(opts.delta >= 0.0 && opts.delta < 0.5)) return fail(nullptr, SHASTA_EINVAL, "need 0 <= delta < 0.5");
   if (opts.delta == 0.0) opts.delta = opts.precision == SHASTA_FP64 ? 1e-10 : 1e-6;

@@ -96,6 +96,11 @@ __device__ __forceinline__ f2 mul2(f2 a, f2 b) { return f2{a.x * b.x, a.y * b.y}
 __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
   return f2{fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y)};
 }
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
 __device__ __forceinline__ float min3f(float a, float b, float c) {
   float r;
   asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
@@ -354,13 +359,10 @@ __device__ __forceinline__ void rec2(f2 E, f2 mx, f2 my, f2 mz, f2 mpar, float o
 // ------------------------------------------------------- antidiffusion ----
 
 // Flux limiter of Sec. 3 on one field: A = s max(0, min(s dhp, |aph|, s dhm))
-// with s = sgn(aph), applied through sign-bit flips (aph = 0 gives 0).
+// with s = sgn(aph) (aph = 0 gives 0), written without the sign: for
+// aph > 0 only the first term can be nonzero, for aph < 0 only the second.
 __device__ __forceinline__ float limit(float aph, float dhp, float dhm) {
-  const uint32_t sg = __float_as_uint(aph) & 0x80000000u;
-  const float p1 = __uint_as_float(__float_as_uint(dhp) ^ sg);
-  const float p2 = __uint_as_float(__float_as_uint(dhm) ^ sg);
-  const float mm = fmaxf(0.0f, min3f(p1, fabsf(aph), p2));
-  return __uint_as_float(__float_as_uint(mm) ^ sg);
+  return fmaxf(min3f(dhp, aph, dhm), 0.0f) + fminf(max3f(dhp, aph, dhm), 0.0f);
 }
 
 // ------------------------------------------------------ line pipeline ----
@@ -393,8 +395,6 @@ __device__ __forceinline__ f2 step2(Line2& s, f2 u, f2 a2, f2 nb2, f2 c2, f2 src
   constexpr int P0 = K & 1, P1 = (K + 1) & 1;  // parity of k (= k-2, k-4) and of k-1 (= k-3)
   // values whose slots are overwritten below are consumed first
   const f2 aph = mul2(eta2, fma2(m8, s.D2[P1], s.Dh[P1]));        // A^ph_{k-3}
-  const f2 sg = f2{copysignf(1.0f, aph.x), copysignf(1.0f, aph.y)};  // +-1
-  const f2 qm = mul2(sg, s.Dh[P0]);                              // s Dh_{k-4}
   const f2 t = add2(s.Uh[P1], s.A[P0]);                          // Uhat_{k-3} + A_{k-4}
   const f2 d = sub2(u, s.Up[P1]);                                // Delta_{k-1}
   // Uhat_{k-1}, the source folded into the innermost term
@@ -402,11 +402,7 @@ __device__ __forceinline__ f2 step2(Line2& s, f2 u, f2 a2, f2 nb2, f2 c2, f2 src
   const f2 dd = sub2(d, s.D[P0]);                                // DD_{k-1}
   const f2 d2 = sub2(dd, s.DD[P0]);                              // D2_{k-2}
   const f2 dh = sub2(uh, s.Uh[P0]);                              // Dh_{k-2}
-  float p0, p1, a0, a1, q0, q1;
-  up(mul2(sg, dh), p0, p1);
-  up(mul2(sg, aph), a0, a1);
-  up(qm, q0, q1);
-  const f2 A = mul2(sg, pk(fmaxf(min3f(p0, a0, q0), 0.0f), fmaxf(min3f(p1, a1, q1), 0.0f)));
+  const f2 A = f2{limit(aph.x, dh.x, s.Dh[P0].x), limit(aph.y, dh.y, s.Dh[P0].y)};
   s.A[P1] = A;
   s.Up[P0] = u;
   s.D[P1] = d;
@@ -561,12 +557,13 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, l
       if (ghost) {
         copy_cell(P, G, dq, dr, G.off() + tr * G.sb(), 1, tr, pos, n);
       } else {
-        const long long c = G.off() + tr * G.sb() + pos;
-        cp_async16(dq, P.qin + 4 * c);
+        const unsigned c = (unsigned)G.off() + (unsigned)tr * (unsigned)G.sb() + (unsigned)pos;
+        cp_async16(dq, P.qin + 4 * (size_t)c);
         cp_async4(dr, P.rin + c);
       }
     }
   };
+  const unsigned base32 = (unsigned)base, stride32 = (unsigned)G.stride();
   // y/z path: own-lane copy of position q into ring slot `slot`
   auto yz_issue = [&](float* slot, int q, bool ghost) {
     float* dq = slot + lane * 4;
@@ -574,8 +571,8 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, l
     if (ghost) {
       copy_cell(P, G, dq, dr, base, G.stride(), tl, q, n);
     } else {
-      const long long c = base + (long long)q * G.stride();
-      cp_async16(dq, P.qin + 4 * c);
+      const unsigned c = base32 + (unsigned)q * stride32;
+      cp_async16(dq, P.qin + 4 * (size_t)c);
       cp_async4(dr, P.rin + c);
     }
   };
@@ -706,11 +703,11 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, l
         sjo[XQ + lane * XRSTR + pj] = oR;
       }
     } else if (valid && jo >= s0 && jo < s1) {
-      const long long c = base + (long long)jo * G.stride();
+      const unsigned c = base32 + (unsigned)jo * stride32;
       float o0, o1, o2, o3;
       up(oA, o0, o1);
       up(oB, o2, o3);
-      *reinterpret_cast<float4*>(P.qout + 4 * c) = make_float4(o0, o1, o2, o3);
+      *reinterpret_cast<float4*>(P.qout + 4 * (size_t)c) = make_float4(o0, o1, o2, o3);
       P.rout[c] = oR;
     }
   };
@@ -770,8 +767,8 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, l
             const int row = r0 + 4 * k;
             const long long tr = g * LANES + row;
             if (tr < G.plane()) {
-              const long long c = G.off() + tr * G.sb() + pos;
-              *reinterpret_cast<float4*>(P.qout + 4 * c) =
+              const unsigned c = (unsigned)G.off() + (unsigned)tr * (unsigned)G.sb() + (unsigned)pos;
+              *reinterpret_cast<float4*>(P.qout + 4 * (size_t)c) =
                   *reinterpret_cast<const float4*>(ring + row * XQSTR + pc * 4);
               P.rout[c] = ring[XQ + row * XRSTR + pc];
             }
