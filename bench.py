@@ -321,7 +321,7 @@ def run_ours(args):
                 "kernel": f"sweep_kernel ({args.precision})",
                 "algorithmic_bytes_per_launch": bytes_per_launch}
 
-    tuning = {"xyz"[a]: {"variant": v, "segments": ns} for a, (v, ns) in enumerate(solver.tuning())}
+    tuning = {"xyz"[a]: {"variant": v, "range_len": r} for a, (v, r) in enumerate(solver.tuning())}
 
     # per-axis sweep durations (after the timed region)
     per_axis = {}

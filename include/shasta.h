@@ -86,8 +86,8 @@ typedef struct shasta_opts {
   int device;    /* CUDA device ordinal */
   int check_input; /* nonzero: set calls scan the state and return
                       SHASTA_EUNPHYSICAL for non-finite values, E < 0 or |M| >= E */
-  int autotune;    /* nonzero: the first shasta_step times launch choices (line
-                      segments, register variant) per axis and keeps the fastest;
+  int autotune;    /* nonzero: the first shasta_step times launch choices (work
+                      range length, register variant) per axis and keeps the fastest;
                       results do not depend on the choice */
   int use_graphs;  /* nonzero: runs of six steps starting at phase 0 replay one
                       captured CUDA graph of 18 sweeps */
@@ -143,13 +143,15 @@ shasta_status shasta_step(shasta_ctx* ctx, int nsteps);
 shasta_status shasta_sweep(shasta_ctx* ctx, int axis);
 
 /* Times the launch choices of the FP32 / MIXED sweep kernels for this grid
- * (segments per line, register variant) and keeps the fastest per axis.
+ * (work range length, register variant) and keeps the fastest per axis.  A
+ * sweep's positions (line groups of 32 lines x positions along the axis) are
+ * cut into equal ranges handed to the resident warps.
  * Runs sweeps from the current state into the spare buffer only, so the
  * state is unchanged; synchronous.  Errors: EINVAL (state not set), ECUDA. */
 shasta_status shasta_autotune(shasta_ctx* ctx);
 
 /* Current launch choice per axis: out[2a] = register variant, out[2a+1] =
- * segments per line (FP64: unused). */
+ * positions per work range (FP64: unused). */
 shasta_status shasta_get_tuning(const shasta_ctx* ctx, int out[6]);
 
 /* Waits until all work enqueued on the context's stream has finished. */

@@ -51,11 +51,11 @@ struct shasta_ctx {
   int sm_count = 152;
   int occ[2][3][2] = {};  // FP32 / MIXED: resident warps per SM [eos][axis][variant]
   int wpb = 4;            // warps per block of the FP32 / MIXED kernels
-  int force_nseg = 0;     // nonzero: segments per line (environment override)
+  long long force_range = 0;  // nonzero: positions per work range (environment override)
   int force_variant = -1; // >= 0: launch variant (environment override)
   bool tuned = false;     // autotuned launch choice below is valid
   int tune_var[3] = {0, 0, 0};
-  int tune_nseg[3] = {1, 1, 1};
+  long long tune_range[3] = {0, 0, 0};
   cudaGraphExec_t graph = nullptr;  // six steps from phase 0, buffer 0
   std::string err;
 };
@@ -158,26 +158,23 @@ shasta_status after_set(shasta_ctx* c) {
   return SHASTA_OK;
 }
 
-// Segment count minimising ceil(items / resident warps) * (length + 13):
-// each segment re-reads a 6-cell halo per side and pays a 7-cell lag.
-int model_nseg(const shasta_ctx* c, int n, long long plane, int wpsm) {
-  const long long groups = (plane + 31) / 32;
-  const long long slots = (long long)c->sm_count * (wpsm > 0 ? wpsm : 1);
-  double best = 1e300;
-  int nseg = 1;
-  const int max_seg = n / 16 > 1 ? n / 16 : 1;
-  for (int k = 1; k <= max_seg && k <= 16; ++k) {
-    const long long waves = (groups * k + slots - 1) / slots;
-    const double cost = (double)waves * ((double)n / k + 13.0);
-    if (cost < best * 0.999) {
-      best = cost;
-      nseg = k;
-    }
-  }
-  return nseg;
+// Positions (line group x position pairs) of a sweep along `axis`.
+long long work_positions(const shasta_ctx* c, int axis) {
+  const long long nx = c->g.nx, ny = c->g.ny, nz = c->g.nz;
+  const long long n = axis == 0 ? nx : (axis == 1 ? ny : nz);
+  const long long plane = axis == 0 ? ny * nz : (axis == 1 ? nx * nz : nx * ny);
+  return (plane + 31) / 32 * n;
 }
 
-SweepParams sweep_params(shasta_ctx* c, int axis, int from, int variant, int nseg) {
+// Range length giving every resident warp of one wave `share` ranges (at
+// least 24 positions: each piece pays a 13-position halo and lag).
+long long range_for(long long total, long long warps, double share) {
+  const double want = (double)warps * share;
+  long long len = (long long)((double)total / (want > 1.0 ? want : 1.0)) + 1;
+  return len < 24 ? 24 : len;
+}
+
+SweepParams sweep_params(shasta_ctx* c, int axis, int from, int variant, long long range) {
   SweepParams P;
   memset(&P, 0, sizeof P);
   long long nx = c->g.nx, ny = c->g.ny, nz = c->g.nz;
@@ -224,13 +221,13 @@ SweepParams sweep_params(shasta_ctx* c, int axis, int from, int variant, int nse
   P.bag_B = c->eos.B;
   P.bag_ec = c->eos.e_c;
   P.clamp_count = c->d_count;
-  P.nseg = nseg < 1 ? 1 : nseg;
-  P.seg_len = (P.n + P.nseg - 1) / P.nseg;
+  P.range_len = range < 1 ? 1 : range;
   P.variant = variant;
   if (c->o.precision != SHASTA_FP64) {
-    // one wave of resident warps loops over the (line group, segment) items
-    const long long items = ((P.plane + 31) / 32) * P.nseg;
-    long long blocks = (items + c->wpb - 1) / c->wpb;
+    // at most one wave of resident warps loops over the ranges
+    const long long total = work_positions(c, axis);
+    const long long ranges = (total + P.range_len - 1) / P.range_len;
+    long long blocks = (ranges + c->wpb - 1) / c->wpb;
     const int wpsm = c->occ[c->eos.kind][axis][variant];
     const long long wave = (long long)c->sm_count * (wpsm > 0 ? wpsm / c->wpb : 1);
     P.blocks = blocks < wave ? blocks : (wave > 0 ? wave : 1);
@@ -239,16 +236,14 @@ SweepParams sweep_params(shasta_ctx* c, int axis, int from, int variant, int nse
 }
 
 // Launch choice of the FP32 / MIXED kernels for an axis: environment
-// overrides, else the autotuned choice, else variant 0 and the model.
-void launch_choice(const shasta_ctx* c, int axis, int& variant, int& nseg) {
+// overrides, else the autotuned choice, else variant 0 and one range per
+// resident warp.
+void launch_choice(const shasta_ctx* c, int axis, int& variant, long long& range) {
   variant = c->tuned ? c->tune_var[axis] : 0;
   if (c->force_variant >= 0) variant = c->force_variant;
-  const int n = axis == 0 ? c->g.nx : (axis == 1 ? c->g.ny : c->g.nz);
-  const long long plane = axis == 0 ? (long long)c->g.ny * c->g.nz
-                                    : (axis == 1 ? (long long)c->g.nx * c->g.nz
-                                                 : (long long)c->g.nx * c->g.ny);
-  nseg = c->tuned ? c->tune_nseg[axis] : model_nseg(c, n, plane, c->occ[c->eos.kind][axis][variant]);
-  if (c->force_nseg > 0) nseg = c->force_nseg;
+  const long long warps = (long long)c->sm_count * c->occ[c->eos.kind][axis][variant];
+  range = c->tuned ? c->tune_range[axis] : range_for(work_positions(c, axis), warps, 1.0);
+  if (c->force_range > 0) range = c->force_range;
 }
 
 cudaError_t launch_params(shasta_ctx* c, int axis, const SweepParams& P) {
@@ -258,9 +253,10 @@ cudaError_t launch_params(shasta_ctx* c, int axis, const SweepParams& P) {
 }
 
 cudaError_t launch_sweep(shasta_ctx* c, int axis) {
-  int variant, nseg;
-  launch_choice(c, axis, variant, nseg);
-  cudaError_t e = launch_params(c, axis, sweep_params(c, axis, c->cur, variant, nseg));
+  int variant;
+  long long range;
+  launch_choice(c, axis, variant, range);
+  cudaError_t e = launch_params(c, axis, sweep_params(c, axis, c->cur, variant, range));
   if (e == cudaSuccess) c->cur ^= 1;
   return e;
 }
@@ -272,7 +268,9 @@ void drop_graph(shasta_ctx* c) {
 
 // Times candidate launch choices per axis with repeated sweeps from the
 // current buffer into the other one (the state itself is not changed) and
-// keeps the fastest.  Segmenting and the variant do not change results.
+// keeps the fastest: the register variant, and ranges of one line group
+// (no line is cut) or of 1/4 .. 3 ranges per resident warp.  The choice
+// does not change results.
 shasta_status autotune(shasta_ctx* c) {
   if (c->o.precision == SHASTA_FP64) {
     c->tuned = true;
@@ -282,14 +280,26 @@ shasta_status autotune(shasta_ctx* c) {
   CK(cudaEventCreate(&e0), "cudaEventCreate");
   CK(cudaEventCreate(&e1), "cudaEventCreate");
   shasta_status st = SHASTA_OK;
+  static const double shares[] = {0.25, 0.5, 1.0, 2.0, 3.0};
   for (int axis = 0; axis < 3 && st == SHASTA_OK; ++axis) {
     const int n = axis == 0 ? c->g.nx : (axis == 1 ? c->g.ny : c->g.nz);
+    const long long total = work_positions(c, axis);
     float best = 1e30f;
-    int bv = 0, bn = 1;
-    const int max_seg = n / 16 > 1 ? n / 16 : 1;
-    for (int var = 0; var < 2; ++var)
-      for (int ns = 1; ns <= max_seg && ns <= 8; ++ns) {
-        SweepParams P = sweep_params(c, axis, c->cur, var, ns);
+    int bv = 0;
+    long long br = n;
+    for (int var = 0; var < 2; ++var) {
+      const long long warps = (long long)c->sm_count * c->occ[c->eos.kind][axis][var];
+      long long cands[6];
+      int nc = 0;
+      cands[nc++] = n;
+      for (double sh : shares) {
+        const long long r = range_for(total, warps, sh);
+        bool dup = false;
+        for (int i = 0; i < nc; ++i) dup = dup || cands[i] == r;
+        if (!dup && r < total) cands[nc++] = r;
+      }
+      for (int ci = 0; ci < nc && st == SHASTA_OK; ++ci) {
+        SweepParams P = sweep_params(c, axis, c->cur, var, cands[ci]);
         cudaError_t ce = cudaSuccess;
         for (int r = 0; r < 2 && ce == cudaSuccess; ++r) ce = launch_params(c, axis, P);
         if (ce == cudaSuccess) ce = cudaEventRecord(e0, c->stream);
@@ -305,11 +315,12 @@ shasta_status autotune(shasta_ctx* c) {
         if (ms < best) {
           best = ms;
           bv = var;
-          bn = ns;
+          br = cands[ci];
         }
       }
+    }
     c->tune_var[axis] = bv;
-    c->tune_nseg[axis] = bn;
+    c->tune_range[axis] = br;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -413,8 +424,8 @@ shasta_status shasta_create(const shasta_grid* g, double dx, double lambda, cons
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) == cudaSuccess && sms > 0)
       c->sm_count = sms;
-    const char* v = getenv("SHASTA_NSEG");
-    if (v && atoi(v) > 0) c->force_nseg = atoi(v);
+    const char* v = getenv("SHASTA_RANGE");
+    if (v && atoll(v) > 0) c->force_range = atoll(v);
     v = getenv("SHASTA_VARIANT");
     if (v && atoi(v) >= 0 && atoi(v) <= 1) c->force_variant = atoi(v);
   }
@@ -578,10 +589,11 @@ shasta_status shasta_autotune(shasta_ctx* c) {
 shasta_status shasta_get_tuning(const shasta_ctx* c, int out[6]) {
   if (!c || !out) return SHASTA_EINVAL;
   for (int a = 0; a < 3; ++a) {
-    int v, ns;
-    launch_choice(c, a, v, ns);
+    int v;
+    long long r;
+    launch_choice(c, a, v, r);
     out[2 * a] = v;
-    out[2 * a + 1] = ns;
+    out[2 * a + 1] = (int)(r < 2147483647LL ? r : 2147483647LL);
   }
   return SHASTA_OK;
 }

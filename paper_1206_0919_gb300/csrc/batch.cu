@@ -44,8 +44,9 @@ struct Event {
 // of the device plan array, swept along `axis`.
 struct LaunchRec {
   int axis = 0, eos = 0, nlist = 0;
-  size_t idx_off = 0, pre_off = 0;
-  long long items = 0;
+  size_t idx_off = 0, pre_off = 0, gpre_off = 0;  // event indices, position / group prefixes
+  long long items = 0;   // positions
+  long long groups = 0;  // line groups
 };
 
 }  // namespace
@@ -80,11 +81,11 @@ struct shasta_batch {
   int sm_count = 152;
   int occ[2][3][2] = {};
   int wpb = 4;
-  // launch choice per axis: register variant and target segment length
-  // (0: lines are not split)
+  // launch choice per axis: register variant and positions per work range
   bool tuned = false;
+  long long force_range = -1;  // >= 0: work range of every axis (environment override; 0 = line groups)
   int tune_var[3] = {0, 0, 0};
-  int tune_len[3] = {0, 0, 0};
+  long long tune_range[3] = {0, 0, 0};  // 0: whole line groups
   // work lists of six consecutive steps (index (steps - plan_base) mod 6)
   bool plan_valid = false;
   int64_t bsteps = 0, plan_base = 0;
@@ -142,15 +143,6 @@ long long plane_of(const shasta_grid& g, int axis) {
                    : (axis == 1 ? (long long)g.nx * g.nz : (long long)g.nx * g.ny);
 }
 
-// Segments per line for a target segment length (0: one segment); at
-// least 16 cells per segment.
-int nseg_for(int n, int len) {
-  if (len <= 0) return 1;
-  int k = (n + len / 2) / len;
-  const int kmax = n / 16 > 1 ? n / 16 : 1;
-  return std::max(1, std::min(k, kmax));
-}
-
 long long groups_of(const Event& e, int axis) { return (plane_of(e.g, axis) + 31) / 32; }
 
 // Resident warps of the machine for a launch choice.
@@ -159,35 +151,37 @@ long long warp_slots(const shasta_batch* b, int eos, int axis, int var) {
   return (long long)b->sm_count * (w > 0 ? w : 1);
 }
 
-// Model of the makespan of one axis over all events for a target segment
-// length: total line positions spread over the resident warps, plus the
-// longest item (the tail); each segment pays a 13-position halo and lag.
-double model_cost(const shasta_batch* b, int axis, int len) {
-  double work = 0, tail = 0;
-  for (const Event& e : b->ev) {
-    if (!e.live) continue;
-    const int n = extent(e.g, axis);
-    const int k = nseg_for(n, len);
-    work += (double)groups_of(e, axis) * (n + 13.0 * k);
-    tail = std::max(tail, (double)n / k + 13.0);
-  }
-  return work / (double)warp_slots(b, 0, axis, 0) + tail;
+// Positions (line group x position pairs) of all live events along an axis.
+long long total_positions(const shasta_batch* b, int axis) {
+  long long t = 0;
+  for (const Event& e : b->ev)
+    if (e.live) t += groups_of(e, axis) * extent(e.g, axis);
+  return t;
 }
 
+// Range length giving every resident warp `share` ranges (at least 24
+// positions: each piece pays a 13-position halo and lag).
+long long range_for(long long total, long long warps, double share) {
+  const double want = (double)warps * share;
+  long long len = (long long)((double)total / (want > 1.0 ? want : 1.0)) + 1;
+  return len < 24 ? 24 : len;
+}
+
+long long total_groups(const shasta_batch* b, int axis) {
+  long long t = 0;
+  for (const Event& e : b->ev)
+    if (e.live) t += groups_of(e, axis);
+  return t;
+}
+
+// Model choice: variant 0; whole line groups (longest lines first, handed
+// out round robin) when there are at least two per resident warp, else one
+// range of positions per resident warp.
 void model_choice(shasta_batch* b) {
-  static const int cands[] = {0, 128, 96, 64, 48, 32};
   for (int a = 0; a < 3; ++a) {
-    double best = 1e300;
-    int bl = 0;
-    for (int len : cands) {
-      const double c = model_cost(b, a, len);
-      if (c < best * 0.999) {
-        best = c;
-        bl = len;
-      }
-    }
+    const long long warps = warp_slots(b, 0, a, 0);
     b->tune_var[a] = 0;
-    b->tune_len[a] = bl;
+    b->tune_range[a] = total_groups(b, a) >= 2 * warps ? 0 : range_for(total_positions(b, a), warps, 1.0);
   }
 }
 
@@ -211,9 +205,8 @@ EosParams eos_params(const shasta_batch* b, const Event& e) {
   return q;
 }
 
-// Descriptor of slot i with the segment counts of the current launch choice
-// (or of `len_override` on axis `ax_override`, for tuning).
-EvDesc desc_of(const shasta_batch* b, int i, int ax_override = -1, int len_override = 0) {
+// Descriptor of slot i.
+EvDesc desc_of(const shasta_batch* b, int i) {
   const Event& e = b->ev[i];
   EvDesc d;
   memset(&d, 0, sizeof d);
@@ -222,8 +215,6 @@ EvDesc desc_of(const shasta_batch* b, int i, int ax_override = -1, int len_overr
   d.ny = e.g.ny;
   d.nz = e.g.nz;
   d.bc = e.g.bc;
-  for (int a = 0; a < 3; ++a)
-    d.nseg[a] = nseg_for(extent(e.g, a), a == ax_override ? len_override : b->tune_len[a]);
   // the same double -> float conversions as the single-event launch
   const double tau_h = 0.5 * e.lambda, tau_f = e.lambda;
   d.tau_h = (float)tau_h;
@@ -250,27 +241,26 @@ int slots_in_use(const shasta_batch* b) {
 
 // Writes the descriptors of all slots in use (synchronous: the pinned copy
 // is reused).
-shasta_status upload_desc(shasta_batch* b, int ax_override = -1, int len_override = 0) {
+shasta_status upload_desc(shasta_batch* b) {
   const int n = slots_in_use(b);
   if (!n) return SHASTA_OK;
   CK(cudaStreamSynchronize(b->stream), "sync");
   for (int i = 0; i < n; ++i)
-    if (b->ev[i].live) b->h_desc[i] = desc_of(b, i, ax_override, len_override);
+    if (b->ev[i].live) b->h_desc[i] = desc_of(b, i);
   CK(cudaMemcpyAsync(b->d_desc, b->h_desc, n * sizeof(EvDesc), cudaMemcpyHostToDevice, b->stream),
      "upload descriptors");
   CK(cudaStreamSynchronize(b->stream), "sync");
   return SHASTA_OK;
 }
 
-// Appends the work list of events `ids` along `axis` (longest items first)
-// to the host plan array.
-LaunchRec make_list(const shasta_batch* b, std::vector<int>& ids, int axis, int eos, int len_axis,
-                    int len, std::vector<int>& out) {
-  auto item_len = [&](int i) {
-    const int n = extent(b->ev[i].g, axis);
-    return (double)n / nseg_for(n, axis == len_axis ? len : b->tune_len[axis]);
-  };
-  std::stable_sort(ids.begin(), ids.end(), [&](int x, int y) { return item_len(x) > item_len(y); });
+// Appends the work list of events `ids` along `axis` to the host plan
+// array, longest lines first: event indices, the prefix of their positions
+// and the prefix of their line groups.
+LaunchRec make_list(const shasta_batch* b, std::vector<int> ids, int axis, int eos,
+                    std::vector<int>& out) {
+  std::stable_sort(ids.begin(), ids.end(), [&](int x, int y) {
+    return extent(b->ev[x].g, axis) > extent(b->ev[y].g, axis);
+  });
   LaunchRec L;
   L.axis = axis;
   L.eos = eos;
@@ -281,11 +271,18 @@ LaunchRec make_list(const shasta_batch* b, std::vector<int>& ids, int axis, int 
   long long acc = 0;
   for (int i : ids) {
     out.push_back((int)acc);
-    const Event& e = b->ev[i];
-    acc += groups_of(e, axis) * nseg_for(extent(e.g, axis), axis == len_axis ? len : b->tune_len[axis]);
+    acc += groups_of(b->ev[i], axis) * extent(b->ev[i].g, axis);
   }
   out.push_back((int)acc);
   L.items = acc;
+  L.gpre_off = out.size();
+  acc = 0;
+  for (int i : ids) {
+    out.push_back((int)acc);
+    acc += groups_of(b->ev[i], axis);
+  }
+  out.push_back((int)acc);
+  L.groups = acc;
   return L;
 }
 
@@ -341,7 +338,7 @@ shasta_status build_plan(shasta_batch* b) {
       for (int a = 0; a < 3; ++a)
         for (int k = 0; k < 2; ++k)
           if (!groups[a][k].empty())
-            b->plan[r][s].push_back(make_list(b, groups[a][k], a, k, -1, 0, host));
+            b->plan[r][s].push_back(make_list(b, groups[a][k], a, k, host));
     }
   shasta_status st = upload_desc(b);
   if (st != SHASTA_OK) return st;
@@ -353,7 +350,8 @@ shasta_status build_plan(shasta_batch* b) {
   return SHASTA_OK;
 }
 
-SweepParams batch_params(const shasta_batch* b, const LaunchRec& L, int from, int variant) {
+SweepParams batch_params(const shasta_batch* b, const LaunchRec& L, int from, int variant,
+                         long long range) {
   SweepParams P;
   memset(&P, 0, sizeof P);
   P.qin = b->quad[from];
@@ -363,25 +361,26 @@ SweepParams batch_params(const shasta_batch* b, const LaunchRec& L, int from, in
   P.eta = b->o.eta;
   P.omd = 1.0 - b->o.delta;
   P.variant = variant;
-  P.nseg = 1;
+  P.range_len = range < 1 ? 0 : range;
   P.plane = 1;
-  // one wave of resident warps loops over the items
+  // at most one wave of resident warps loops over the ranges (or groups)
   const long long wave = warp_slots(b, L.eos, L.axis, variant) / b->wpb;
-  const long long need = (L.items + b->wpb - 1) / b->wpb;
+  const long long ranges = range < 1 ? L.groups : (L.items + P.range_len - 1) / P.range_len;
+  const long long need = (ranges + b->wpb - 1) / b->wpb;
   P.blocks = std::max(1LL, std::min(need, wave));
   return P;
 }
 
 cudaError_t launch_rec(shasta_batch* b, const LaunchRec& L, int from, int variant,
-                       cudaStream_t st = nullptr) {
+                       long long range, cudaStream_t st = nullptr) {
   if (!L.nlist || !L.items) return cudaSuccess;
   if (!st) st = b->stream;
   ++b->launches;
-  const SweepParams P = batch_params(b, L, from, variant);
+  const SweepParams P = batch_params(b, L, from, variant, range);
   BatchList BL;
   BL.ev = b->d_desc;
   BL.idx = b->d_plan + L.idx_off;
-  BL.prefix = b->d_plan + L.pre_off;
+  BL.prefix = b->d_plan + (range < 1 ? L.gpre_off : L.pre_off);
   BL.nlist = L.nlist;
   return b->mixed ? launch_batch_mixed(P, BL, L.axis, L.eos, st)
                   : launch_batch_f32(P, BL, L.axis, L.eos, st);
@@ -400,7 +399,7 @@ cudaError_t launch_step(shasta_batch* b, int r) {
     for (size_t i = 0; i < V.size() && e == cudaSuccess; ++i) {
       const int k = (int)i - 1;  // launch 0 on the batch stream, the others on side streams
       cudaStream_t st = k >= 0 && k < nside ? b->side[k] : b->stream;
-      e = launch_rec(b, V[i], b->cur, b->tune_var[V[i].axis], st);
+      e = launch_rec(b, V[i], b->cur, b->tune_var[V[i].axis], b->tune_range[V[i].axis], st);
     }
     for (int i = 0; i < nside && e == cudaSuccess; ++i) {
       e = cudaEventRecord(b->join[i], b->side[i]);
@@ -412,41 +411,44 @@ cudaError_t launch_step(shasta_batch* b, int r) {
   return cudaSuccess;
 }
 
-// Times (variant, segment length) per axis: every event sweeps along the
+// Times (variant, range length) per axis: every event sweeps along the
 // axis from the current buffer into the other one (the state is not
-// changed).  Segmenting and the variant do not change results.
+// changed).  The launch choice does not change results.
 shasta_status autotune(shasta_batch* b) {
   if (!b->nlive) return SHASTA_OK;
-  static const int lens[] = {0, 96, 48};
+  static const double shares[] = {0.0, 0.5, 1.0, 2.0};
+  const int64_t launches0 = b->launches;  // trial launches are not counted
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0), "cudaEventCreate");
   CK(cudaEventCreate(&e1), "cudaEventCreate");
-  shasta_status st = SHASTA_OK;
+  shasta_status st = upload_desc(b);
   const int n = slots_in_use(b);
   for (int a = 0; a < 3 && st == SHASTA_OK; ++a) {
+    std::vector<int> host;
+    std::vector<LaunchRec> recs;
+    for (int k = 0; k < 2; ++k) {
+      std::vector<int> ids;
+      for (int i = 0; i < n; ++i)
+        if (b->ev[i].live && b->ev[i].eos.kind == k) ids.push_back(i);
+      if (!ids.empty()) recs.push_back(make_list(b, ids, a, k, host));
+    }
+    st = upload_plan(b, host);
+    if (st != SHASTA_OK) break;
+    const long long total = total_positions(b, a);
     float best = 1e30f;
-    int bv = 0, bl = 0;
-    for (int len : lens) {
-      st = upload_desc(b, a, len);
-      if (st != SHASTA_OK) break;
-      std::vector<int> host;
-      std::vector<LaunchRec> recs;
-      for (int k = 0; k < 2; ++k) {
-        std::vector<int> ids;
-        for (int i = 0; i < n; ++i)
-          if (b->ev[i].live && b->ev[i].eos.kind == k) ids.push_back(i);
-        if (!ids.empty()) recs.push_back(make_list(b, ids, a, k, a, len, host));
-      }
-      st = upload_plan(b, host);
-      if (st != SHASTA_OK) break;
-      for (int var = 0; var < 2; ++var) {
+    int bv = 0;
+    long long br = b->tune_range[a];
+    for (int var = 0; var < 2 && st == SHASTA_OK; ++var)
+      for (double sh : shares) {
+        // share 0: whole line groups
+        const long long range = sh > 0 ? range_for(total, warp_slots(b, 0, a, var), sh) : 0;
         cudaError_t ce = cudaSuccess;
         for (const LaunchRec& L : recs)
-          if (ce == cudaSuccess) ce = launch_rec(b, L, b->cur, var);
+          if (ce == cudaSuccess) ce = launch_rec(b, L, b->cur, var, range);
         if (ce == cudaSuccess) ce = cudaEventRecord(e0, b->stream);
         for (int rep = 0; rep < 3 && ce == cudaSuccess; ++rep)
           for (const LaunchRec& L : recs)
-            if (ce == cudaSuccess) ce = launch_rec(b, L, b->cur, var);
+            if (ce == cudaSuccess) ce = launch_rec(b, L, b->cur, var, range);
         if (ce == cudaSuccess) ce = cudaEventRecord(e1, b->stream);
         if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
         float ms = 0;
@@ -458,15 +460,15 @@ shasta_status autotune(shasta_batch* b) {
         if (ms < best) {
           best = ms;
           bv = var;
-          bl = len;
+          br = range;
         }
       }
-    }
     b->tune_var[a] = bv;
-    b->tune_len[a] = bl;
+    b->tune_range[a] = br;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  b->launches = launches0;
   b->plan_valid = false;
   if (st == SHASTA_OK) b->tuned = true;
   return st;
@@ -565,6 +567,8 @@ shasta_status shasta_batch_create(const shasta_batch_opts* o, shasta_batch** out
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) == cudaSuccess && sms > 0)
       b->sm_count = sms;
+    const char* v = getenv("SHASTA_BATCH_RANGE");
+    if (v && atoll(v) >= 0) b->force_range = atoll(v);
   }
   auto bail = [&](cudaError_t err, const char* where) {
     std::string m = std::string(where) + ": " + cudaGetErrorString(err);
@@ -751,10 +755,12 @@ shasta_status shasta_batch_step(shasta_batch* b, int nsteps) {
   DeviceGuard dg(b->device);
   if (!b->tuned) {
     model_choice(b);
-    if (b->o.autotune) {
+    if (b->o.autotune && b->force_range < 0) {
       shasta_status st = autotune(b);
       if (st != SHASTA_OK) return st;
     }
+    if (b->force_range >= 0)
+      for (int a = 0; a < 3; ++a) b->tune_range[a] = b->force_range;
     b->tuned = true;
     b->plan_valid = false;
   }

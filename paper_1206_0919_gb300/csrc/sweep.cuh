@@ -59,8 +59,8 @@ struct SweepParams {
   double omd;             // 1 - delta (clamp of |M|)
   double bag_B, bag_ec;
   unsigned long long* clamp_count;  // cells recovered with |M| clamped or E <= 0
-  int seg_len;                      // fast kernels: cells per line segment (multiple of 8)
-  int nseg;                         // fast kernels: segments per line
+  long long range_len;              // fast kernels: positions per work range (>= 1; batches: 0
+                                    // = whole line groups, BatchList.prefix then counts groups)
   int variant;                      // fast kernels: launch variant (0: capped registers, 1: not)
   long long blocks;                 // fast kernels: grid size (one wave of resident warps)
   // fast kernels: state as (E, Mx, My, Mz) quads per cell plus an R array
@@ -76,8 +76,6 @@ struct SweepParams {
 struct EvDesc {
   long long off;
   int nx, ny, nz, bc;
-  int nseg[3];                      // segments per line along each axis
-  int pad;
   float tau_h, tau_f;               // lambda/2 and lambda
   float htau_h, htau_f;             // half of each
   float bag_B, bag_ec;
@@ -85,8 +83,10 @@ struct EvDesc {
   unsigned long long* clamp_count;  // the event's clamp counter
 };
 
-// Work list of one batched launch: list entry k is event idx[k], whose work
-// items (line group, segment) are numbered prefix[k] .. prefix[k+1]-1.
+// Work list of one batched launch: list entry k is event idx[k], whose
+// (line group, position) pairs along the axis are numbered prefix[k] ..
+// prefix[k+1]-1 (group-major: ceil(lines / 32) groups of n positions), or,
+// when the launch takes whole line groups, whose line groups are.
 struct BatchList {
   const EvDesc* ev;
   const int* idx;

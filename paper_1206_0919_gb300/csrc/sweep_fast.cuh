@@ -7,9 +7,11 @@
 //  * State layout: (E, Mx, My, Mz) as one 16-byte quad per cell and R as a
 //    separate array.  A cell moves with one 16-byte and one 4-byte access,
 //    and the quad splits into the register pairs (E, Mx), (My, Mz).
-//  * One warp streams 32 lines (one per lane) along the sweep axis.  Lines
-//    may be cut into segments (each with its own 6-cell halo per side) so
-//    that small grids still fill the machine.
+//  * One warp streams 32 lines (one per lane) along the sweep axis.  The
+//    positions of all line groups are cut into equal ranges, one or more
+//    per warp, so that every warp has the same amount of work; a range
+//    touches one or two line groups (each piece with its own 6-cell halo
+//    per side).
 //  * Input cells are staged through a per-warp shared-memory ring filled
 //    with cp.async ahead of use.  For y/z sweeps each lane copies its own
 //    line (the lanes of one position are adjacent in memory).  For x sweeps
@@ -44,7 +46,7 @@
 //  * The including units are built with -fmad=false: every fused
 //    multiply-add is explicit, so all instantiations of the streaming step
 //    (position parity, boundary variant, register variant) round alike and
-//    the result does not depend on how lines are cut into segments.
+//    the result does not depend on how lines are cut into pieces.
 #pragma once
 
 #include <type_traits>
@@ -162,7 +164,7 @@ struct ItemGeo {
   long long stride;  // cell stride along the line
   long long plane;   // lines along this axis
   long long sb, sc;  // first cell of line t = b + nb*c: off + b*sb + c*sc
-  int n, nb, bc, nseg;
+  int n, nb, bc;
   const float* frozen;
   float tau_h, tau_f, htau_h, htau_f, B, ec;
   unsigned long long* clamp;
@@ -181,7 +183,6 @@ struct GeoP {
   __device__ __forceinline__ int n() const { return P.n; }
   __device__ __forceinline__ int nb() const { return P.nb; }
   __device__ __forceinline__ int bc() const { return P.bc; }
-  __device__ __forceinline__ int nseg() const { return P.nseg; }
   __device__ __forceinline__ const float* frozen() const { return static_cast<const float*>(P.frozen); }
   __device__ __forceinline__ float tau_h() const { return float(P.tau_h); }
   __device__ __forceinline__ float tau_f() const { return float(P.tau_f); }
@@ -200,7 +201,6 @@ struct GeoR {
   __device__ __forceinline__ int n() const { return g.n; }
   __device__ __forceinline__ int nb() const { return g.nb; }
   __device__ __forceinline__ int bc() const { return g.bc; }
-  __device__ __forceinline__ int nseg() const { return g.nseg; }
   __device__ __forceinline__ const float* frozen() const { return g.frozen; }
   __device__ __forceinline__ float tau_h() const { return g.tau_h; }
   __device__ __forceinline__ float tau_f() const { return g.tau_f; }
@@ -238,7 +238,6 @@ __device__ __forceinline__ ItemGeo geo_of(const EvDesc& D) {
     G.sc = nx;
   }
   G.bc = D.bc;
-  G.nseg = D.nseg[AXIS];
   G.frozen = D.frozen[AXIS];
   G.tau_h = D.tau_h;
   G.tau_f = D.tau_f;
@@ -498,28 +497,20 @@ using bc_ = std::integral_constant<bool, V>;
 //   half-step pass of (E, M) with newest cell q      -> U^h_{q-3}
 //   full-step pass of (E, M, R) with newest cell q-4 -> U^{n+1}_{q-7}
 
-// One work item: line group g, segment seg of the event described by G.
+// One piece of work: positions [s0, s1) of the 32 lines of line group g of
+// the event described by G (x path: s0 and, unless s1 = n, s1 on 8-cell
+// chunk boundaries).
 template <int EOS, int AXIS, bool MIXED, int RING, int DIST, class Geo>
-__device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, long long local,
+__device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, int g, int s0, int s1,
                                            float* wsm, int lane, unsigned& nclamp) {
   constexpr bool XP = AXIS == 0;
   constexpr int LAG = 7;
   static_assert(RING == 8 && DIST == 3, "ring layout assumes 8 slots, 3 ahead");
   const int n = G.n();
-  const long long ngroups = (G.plane() + LANES - 1) / LANES;
-  const long long g = local % ngroups;
-  const int seg = (int)(local / ngroups);
-  const long long t = g * LANES + lane;
+  const long long t = (long long)g * LANES + lane;
   const bool valid = t < G.plane();
   const long long tl = valid ? t : G.plane() - 1;
   const long long base = G.off() + (tl % G.nb()) * G.sb() + (tl / G.nb()) * G.sc();  // first cell of the line
-  // segments split the line evenly (x path: on 8-cell chunk boundaries)
-  int s0 = (int)(((long long)seg * n) / G.nseg());
-  int s1 = (int)(((long long)(seg + 1) * n) / G.nseg());
-  if (XP) {
-    s0 &= ~(CH - 1);
-    s1 = seg + 1 == G.nseg() ? n : (s1 & ~(CH - 1));
-  }
   // positions streamed: qs .. qe (the x path starts on a chunk boundary)
   const int qs = XP ? ((s0 - 2 * NG) & ~(CH - 1)) : s0 - 2 * NG;
   const int qe = s1 + LAG - 1;
@@ -783,43 +774,97 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, l
   __syncwarp();
 }
 
-// The work items of one launch, (line group, segment) of the single event
-// of P or of the events of the work list L (BATCH), taken by the warps in a
-// grid stride.
+// Work of one launch: the positions of all line groups of the single event
+// of P, or of the events of the work list L (BATCH), numbered group by group
+// (event after event) and cut into ranges of P.range_len positions; warp w
+// takes ranges w, w + warps, ...  A range is streamed piece by piece (one
+// piece per line group it touches, each with its own halo); on the x path
+// range boundaries are moved down to 8-cell chunk boundaries of their line.
+// A batch may instead take whole line groups as work units (range_len 0).
 template <int EOS, int AXIS, bool MIXED, int WARPS, int RING, int DIST, bool BATCH>
 __device__ __forceinline__ void sweep_items(const SweepParams& P, const BatchList& L) {
+  constexpr bool XP = AXIS == 0;
   extern __shared__ __align__(16) float smem[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   float* wsm = smem + (size_t)warp * Smem<AXIS, RING>::per_warp;
-  const long long nwarps = (long long)gridDim.x * WARPS;
-  const long long first = (long long)blockIdx.x * WARPS + warp;
+  // position counts of one launch stay below 2^31 (checked on the host)
+  const int nwarps = (int)gridDim.x * WARPS;
+  const int first = (int)blockIdx.x * WARPS + warp;
+  const int len = (int)P.range_len;
   unsigned nclamp = 0;
   if constexpr (BATCH) {
-    const long long nitems = L.nlist > 0 ? L.prefix[L.nlist] : 0;
-#pragma unroll 1
-    for (long long item = first; item < nitems; item += nwarps) {
-      // list entry of the item: the largest k with prefix[k] <= item
+    const int total = L.nlist > 0 ? L.prefix[L.nlist] : 0;
+    // list entry holding position x: the largest k with prefix[k] <= x
+    auto entry = [&](int x) {
       int lo = 0, hi = L.nlist - 1;
 #pragma unroll 1
       while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (L.prefix[mid] <= item)
+        if (L.prefix[mid] <= x)
           lo = mid;
         else
           hi = mid - 1;
       }
-      const GeoR G{geo_of<AXIS>(L.ev[L.idx[lo]])};
-      sweep_item<EOS, AXIS, MIXED, RING, DIST>(P, G, item - L.prefix[lo], wsm, lane, nclamp);
-      if (nclamp && G.g.clamp) atomicAdd(G.g.clamp, (unsigned long long)nclamp);
-      nclamp = 0;
+      return lo;
+    };
+    auto bound = [&](int x) -> int {
+      if (!XP || x >= total) return x;
+      const int k = entry(x);
+      return x - ((x - L.prefix[k]) % L.ev[L.idx[k]].nx) % CH;
+    };
+    if (len <= 0) {
+      // line-group mode: prefix counts line groups; a work unit is one
+      // whole line group
+#pragma unroll 1
+      for (int r = first; r < total; r += nwarps) {
+        const int k = entry(r);
+        const GeoR G{geo_of<AXIS>(L.ev[L.idx[k]])};
+        sweep_item<EOS, AXIS, MIXED, RING, DIST>(P, G, r - L.prefix[k], 0, G.n(), wsm, lane, nclamp);
+        if (nclamp && G.g.clamp) atomicAdd(G.g.clamp, (unsigned long long)nclamp);
+        nclamp = 0;
+      }
+      return;
+    }
+    const int nranges = (total + len - 1) / len;
+#pragma unroll 1
+    for (int r = first; r < nranges; r += nwarps) {
+      int x = bound(r * len);
+      const int end = bound(min(r * len + len, total));
+#pragma unroll 1
+      while (x < end) {
+        const int k = entry(x);
+        const GeoR G{geo_of<AXIS>(L.ev[L.idx[k]])};
+        const int n = G.n();
+        const int loc = x - L.prefix[k];
+        const int g = loc / n;
+        const int s0 = loc - g * n;
+        const int pe = min(end, x - s0 + n);  // the piece ends with the range or the line group
+        sweep_item<EOS, AXIS, MIXED, RING, DIST>(P, G, g, s0, s0 + (pe - x), wsm, lane, nclamp);
+        if (nclamp && G.g.clamp) atomicAdd(G.g.clamp, (unsigned long long)nclamp);
+        nclamp = 0;
+        x = pe;
+      }
     }
   } else {
     const GeoP G{P};
-    const long long nitems = ((P.plane + LANES - 1) / LANES) * P.nseg;
+    const int n = P.n;
+    const int total = (int)((P.plane + LANES - 1) / LANES) * n;
+    auto bound = [&](int x) -> int { return XP && x < total ? x - (x % n) % CH : x; };
+    const int nranges = (total + len - 1) / len;
 #pragma unroll 1
-    for (long long item = first; item < nitems; item += nwarps)
-      sweep_item<EOS, AXIS, MIXED, RING, DIST>(P, G, item, wsm, lane, nclamp);
+    for (int r = first; r < nranges; r += nwarps) {
+      int x = bound(r * len);
+      const int end = bound(min(r * len + len, total));
+#pragma unroll 1
+      while (x < end) {
+        const int g = x / n;
+        const int s0 = x - g * n;
+        const int pe = min(end, x - s0 + n);
+        sweep_item<EOS, AXIS, MIXED, RING, DIST>(P, G, g, s0, s0 + (pe - x), wsm, lane, nclamp);
+        x = pe;
+      }
+    }
     if (nclamp && P.clamp_count) atomicAdd(P.clamp_count, (unsigned long long)nclamp);
   }
 }

@@ -45,9 +45,15 @@ def capacity(events, extra=0):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "mixed"])
-@pytest.mark.parametrize("graphs,tune", [(True, True), (False, False)])
-def test_batch_matches_single_bitwise(precision, graphs, tune):
+@pytest.mark.parametrize("graphs,tune,rng", [(True, True, None), (False, False, None),
+                                             (True, False, "0"), (False, False, "19")])
+def test_batch_matches_single_bitwise(monkeypatch, precision, graphs, tune, rng):
+    """rng forces the work decomposition: "0" whole line groups, "19"
+    ranges of 19 positions (lines cut at arbitrary and chunk-rounded
+    places, across event boundaries)."""
     require_gpu()
+    if rng is not None:
+        monkeypatch.setenv("SHASTA_BATCH_RANGE", rng)
     with S.Batch(capacity(EVENTS), precision=precision, use_graphs=graphs,
                  autotune=tune) as b:
         ids, prims = [], []

@@ -197,15 +197,16 @@ def test_full_size_one_step_fp32():
 @pytest.mark.parametrize("precision", ["fp32", "mixed"])
 @pytest.mark.parametrize("bc", [OR.BC_REFLECT, OR.BC_PERIODIC, OR.BC_FROZEN])
 @pytest.mark.parametrize("eos", [OR.EOS_IDEAL, OR.EOS_BAG])
-@pytest.mark.parametrize("shape,nseg", [((37, 21, 13), 0), ((64, 40, 9), 3), ((3, 5, 2), 0),
-                                        ((40, 1, 1), 0), ((1, 33, 1), 0), ((2, 1, 29), 0),
-                                        ((70, 66, 65), 2), ((97, 35, 8), 5)])
-def test_fp32_random_states(monkeypatch, shape, nseg, bc, eos, precision):
-    """The FP32 kernels on ragged shapes, forced line segmentation (several
-    segments per line, halo re-read), short lines, every boundary rule and
-    both EoS: relative L1 error per field against the FP64 oracle."""
-    if nseg:
-        monkeypatch.setenv("SHASTA_NSEG", str(nseg))
+@pytest.mark.parametrize("shape,rng", [((37, 21, 13), 0), ((64, 40, 9), 29), ((3, 5, 2), 0),
+                                       ((40, 1, 1), 0), ((1, 33, 1), 0), ((2, 1, 29), 0),
+                                       ((70, 66, 65), 45), ((97, 35, 8), 17), ((33, 9, 20), 1)])
+def test_fp32_random_states(monkeypatch, shape, rng, bc, eos, precision):
+    """The FP32 kernels on ragged shapes, forced work ranges (lines cut into
+    pieces at arbitrary and chunk-rounded positions, halos re-read, ranges
+    of one position), short lines, every boundary rule and both EoS:
+    relative L1 error per field against the FP64 oracle."""
+    if rng:
+        monkeypatch.setenv("SHASTA_RANGE", str(rng))
     pr = W.random_state(shape, seed=sum(shape) + 10 * bc + 100 * eos, vmax=0.6,
                         e_range=(0.3, 3.0) if eos == OR.EOS_BAG else (0.05, 5.0))
     O = oracle()
@@ -255,8 +256,8 @@ def test_graphs_and_launch_choices_bitwise(monkeypatch, precision):
     ref = run(autotune=False, use_graphs=False)
     outs = [run(autotune=True, use_graphs=True)]
     if precision != "fp64":
-        for nseg, var in ((1, 0), (3, 1), (4, 0)):
-            monkeypatch.setenv("SHASTA_NSEG", str(nseg))
+        for rng, var in ((100000, 0), (37, 1), (24, 0), (5, 1)):
+            monkeypatch.setenv("SHASTA_RANGE", str(rng))
             monkeypatch.setenv("SHASTA_VARIANT", str(var))
             outs.append(run(autotune=False, use_graphs=True))
     for out in outs:
@@ -276,4 +277,4 @@ def test_autotune_keeps_state():
         tune = s.tuning()
     for a, b in zip(before, after):
         assert np.array_equal(a, b)
-    assert all(v in (0, 1) and ns >= 1 for v, ns in tune)
+    assert all(v in (0, 1) and r >= 1 for v, r in tune)
