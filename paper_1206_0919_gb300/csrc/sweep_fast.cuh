@@ -534,23 +534,30 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, i
 
   auto x_slot = [&](int C) -> float* { return wsm + ((C + 3 * 4) % XSLOTS) * XSLOT; };
   // x path: cooperative copy of chunk C = positions [8C, 8C+8) of 32 rows
+  // (the ghost variant, rare, stays a rolled loop: the x kernel is
+  // sensitive to code size)
   auto x_issue = [&](int C, bool ghost) {
     float* ring = x_slot(C);
     const int r0 = lane >> 3, pc = lane & 7;
     const int pos = C * CH + pc;
+    if (ghost) {
+#pragma unroll 1
+      for (int k = 0; k < 8; ++k) {
+        const int row = r0 + 4 * k;
+        long long tr = g * LANES + row;
+        tr = tr < G.plane() ? tr : G.plane() - 1;
+        copy_cell(P, G, ring + row * XQSTR + pc * 4, ring + XQ + row * XRSTR + pc,
+                  G.off() + tr * G.sb(), 1, tr, pos, n);
+      }
+    } else {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int row = r0 + 4 * k;
-      long long tr = g * LANES + row;
-      tr = tr < G.plane() ? tr : G.plane() - 1;
-      float* dq = ring + row * XQSTR + pc * 4;
-      float* dr = ring + XQ + row * XRSTR + pc;
-      if (ghost) {
-        copy_cell(P, G, dq, dr, G.off() + tr * G.sb(), 1, tr, pos, n);
-      } else {
+      for (int k = 0; k < 8; ++k) {
+        const int row = r0 + 4 * k;
+        long long tr = g * LANES + row;
+        tr = tr < G.plane() ? tr : G.plane() - 1;
         const unsigned c = (unsigned)G.off() + (unsigned)tr * (unsigned)G.sb() + (unsigned)pos;
-        cp_async16(dq, P.qin + 4 * (size_t)c);
-        cp_async4(dr, P.rin + c);
+        cp_async16(ring + row * XQSTR + pc * 4, P.qin + 4 * (size_t)c);
+        cp_async4(ring + XQ + row * XRSTR + pc, P.rin + c);
       }
     }
   };
@@ -753,7 +760,7 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, i
         const int r0 = lane >> 3, pc = lane & 7;
         const int pos = fl + pc;
         if (pos < avail) {
-#pragma unroll
+#pragma unroll 2
           for (int k = 0; k < 8; ++k) {
             const int row = r0 + 4 * k;
             const long long tr = g * LANES + row;
