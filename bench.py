@@ -52,10 +52,12 @@ def parse():
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--mode", choices=["full", "kernels"], default="full",
                     help="kernels: only warmup + K steps (for profiler captures)")
-    ap.add_argument("--workload", choices=["single", "batch64", "serve"], default="single",
+    ap.add_argument("--workload", choices=["single", "batch64", "serve", "tube64", "blast512"],
+                    default="single",
                     help="single: one 200^3 hot-spot event (the headline); batch64: 64 events "
                          "of sizes from {48,64,96,128,160}^3 advanced as one batch; serve: a "
-                         "Poisson stream of events through the serving loop")
+                         "Poisson stream of events through the serving loop; tube64: the 64^3 "
+                         "FP64 shock tube, 40 steps; blast512: the 512^3 blast, 500 steps")
     ap.add_argument("--events", type=int, default=None,
                     help="batch64: events in the batch (64); serve: events per rank (300)")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: arrivals per second per rank")
@@ -678,6 +680,84 @@ def run_serve(args):
     return 0
 
 
+# ------------------------------------------------------- small / large ----
+
+def timed_steps(solver, stream, k):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def run_fixed(args):
+    """tube64: the 64^3 planar shock tube, FP64 (and FP32 beside it), 40
+    steps; blast512: the 512^3 spherical blast, FP32 and MIXED for 500 steps
+    and FP64 timed over 10 steps, with the drift of the E and R totals."""
+    import torch
+
+    from paper_1206_0919_gb300 import shasta as S
+    from paper_1206_0919_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    if args.workload == "tube64":
+        N, steps, prims = 64, 40, W.shock_tube(64, 64, 64)
+        cfg = {"workload": "shock_tube_64^3", "grid": [N] * 3, "steps": steps, "precision": "fp64",
+               "e_L": 1.0, "e_R": 0.01, "n_L": 1.0, "n_R": 0.01, "lambda": 0.4, "eta": 0.125,
+               "bc": "reflect", "eos": "ideal p=e/3", "data": "synthetic"}
+        legs = (("fp64", steps), ("fp32", steps))
+    else:
+        N, steps, prims = 512, 500, W.blast(N=512, radius=40.0)
+        cfg = {"workload": "blast_512^3", "grid": [N] * 3, "steps": steps, "radius": 40,
+               "e_in": 1e3, "e_out": 0.1, "lambda": 0.4, "eta": 0.125, "bc": "reflect",
+               "eos": "ideal p=e/3", "data": "synthetic"}
+        legs = (("fp32", steps), ("mixed", steps), ("fp64", 10))
+    ncell = N ** 3
+    out = {}
+    for prec, k in legs:
+        with S.Solver((N, N, N), precision=prec, stream=stream.cuda_stream, device=local) as s:
+            s.set_primitives(*prims.as_list())
+            t0 = s.totals()
+            s.autotune()
+            secs = timed_steps(s, stream, k)
+            t1 = s.totals()
+            out[prec] = {"value": ncell * k / secs, "unit": UNIT, "steps": k,
+                         "ms_per_step": secs * 1e3 / k,
+                         "drift_E": abs(t1[0] - t0[0]) / abs(t0[0]),
+                         "drift_R": abs(t1[4] - t0[4]) / abs(t0[4]), "clamps": s.counters()}
+    main_prec = legs[0][0]
+    cpu = None
+    if args.workload == "tube64" and not args.no_cpu_baseline:
+        from oracle import oracle as OR
+        O = OR.default()
+        O.set_threads(os.cpu_count() or 1)
+        P = OR.params((N, N, N))
+        U = O.prim2cons(P, *prims.as_list())
+        t = time.perf_counter()
+        O.step(P, U, steps)
+        dt = time.perf_counter() - t
+        cpu = {"value": ncell * steps / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"the whole workload ({steps} oracle steps, {dt:.1f} s)"}
+    if rank == 0:
+        word = 8 if main_prec == "fp64" else 4
+        line = {"metric": METRIC, "value": out[main_prec]["value"], "unit": UNIT, "n_gpus": 1,
+                "steps": out[main_prec]["steps"], "warmup": 0,
+                "ms_per_step": out[main_prec]["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp32": "f32", "fp64": "f64"}[main_prec], "data": "synthetic",
+                "config": cfg, "legs": out, "cpu_baseline": cpu,
+                "roofline": {"bound": "hbm", "achieved": ncell * 10 * word * 3 /
+                             (out[main_prec]["ms_per_step"] / 1e3) / 1e9,
+                             "peak": measured_peak()[0], "unit": "GB/s"}}
+        line["roofline"]["frac"] = line["roofline"]["achieved"] / line["roofline"]["peak"]
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -688,6 +768,8 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload in ("tube64", "blast512"):
+        return run_fixed(args)
     return run_ours(args)
 
 

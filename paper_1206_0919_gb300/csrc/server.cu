@@ -288,6 +288,10 @@ bool admit(shasta_server* s) {
   return true;
 }
 
+// One round: admit the events copied in during the previous round, take
+// finished ones out, enqueue the next steps, and while they run copy the
+// next queue heads in (first come first served, while slots, pool room and
+// input staging allow), then wait for the steps.
 void worker_main(shasta_server* s) {
   cudaSetDevice(s->o.device);
   double tp[7] = {};  // [4] (copy out) is kept by the deliverer
@@ -298,7 +302,6 @@ void worker_main(shasta_server* s) {
     mark = t;
   };
   for (;;) {
-    std::vector<JobP> to_stage;
     {
       std::unique_lock<std::mutex> lk(s->mu);
       for (int k = 0; k < 7; ++k)
@@ -310,9 +313,34 @@ void worker_main(shasta_server* s) {
         lap(6);
         continue;
       }
-      // first come first served: stage queue heads while slots, pool room
-      // (largest free run less what staged events will take) and staging
-      // memory allow
+    }
+    if (!admit(s)) break;
+    lap(1);
+    if (!harvest(s)) break;
+    lap(2);
+    if (!s->resident.empty()) {
+      int64_t k = s->o.steps_per_round;
+      for (const JobP& j : s->resident) k = std::min(k, j->steps_left);
+      if (shasta_batch_step(s->batch, (int)k) != SHASTA_OK) {
+        stop_all(s, batch_msg(s, "step"));
+        break;
+      }
+      for (const JobP& j : s->resident) {
+        j->steps_left -= k;
+        j->steps += k;
+      }
+      int64_t info[7] = {};
+      shasta_batch_info(s->batch, info);
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->batch_steps += k;
+      s->sweep_launches = info[6];
+    }
+    lap(3);
+    // copy the next events in while the steps run
+    std::vector<JobP> to_stage;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      // pool room: the largest free run less what staged events will take
       int64_t info[7] = {};
       shasta_batch_info(s->batch, info);
       long long room = info[3];
@@ -343,29 +371,8 @@ void worker_main(shasta_server* s) {
       if (!ok) break;
       s->staged.push_back(j);
     }
+    if (!ok) break;
     lap(0);
-    if (!ok || !admit(s)) break;
-    lap(1);
-    if (!harvest(s)) break;
-    lap(2);
-    if (!s->resident.empty()) {
-      int64_t k = s->o.steps_per_round;
-      for (const JobP& j : s->resident) k = std::min(k, j->steps_left);
-      if (shasta_batch_step(s->batch, (int)k) != SHASTA_OK) {
-        stop_all(s, batch_msg(s, "step"));
-        break;
-      }
-      for (const JobP& j : s->resident) {
-        j->steps_left -= k;
-        j->steps += k;
-      }
-      int64_t info[7] = {};
-      shasta_batch_info(s->batch, info);
-      std::lock_guard<std::mutex> lk(s->mu);
-      s->batch_steps += k;
-      s->sweep_launches = info[6];
-    }
-    lap(3);
     if (shasta_batch_sync(s->batch) != SHASTA_OK) {
       stop_all(s, batch_msg(s, "sync"));
       break;

@@ -1,0 +1,175 @@
+"""Parity at the full workload sizes, in the launch configuration the
+benchmark times (autotuned launch choice, six-step CUDA graphs).
+
+* 200^3 hot spots (the benchmark's workload): FP32 and MIXED against the
+  FP64 oracle run on all host cores.  The stated FP32 bar (relative L1
+  error of e <= 1e-4) holds through 75 steps.  This flow amplifies
+  rounding-size perturbations about 1e5-fold by step 200: even the FP64
+  oracle started from the FP32-rounded initial state ends 2.5e-3 away from
+  itself (tests/golden/sensitivity.json).  At 200 steps the FP32 error must
+  stay within ten times that envelope, and the conserved totals within
+  1e-5 of the oracle's and of their initial values (E, R).
+* 64 uneven events in one batch, 100 steps (MIXED): the smallest events of
+  the batch against the oracle, cell by cell (<= 1e-4).
+* 512^3 blast, 500 steps: the totals of E and R in the closed box
+  (reflecting walls) stay within 1e-5 of their initial values.  The same
+  setup at 128^3 (radius 10 cells) against the oracle at the FP32 path's
+  clamp margin (delta = 1e-6): <= 1e-4 through 50 steps; at 125 steps
+  within three times the change the clamp margin alone causes in the FP64
+  oracle (delta 1e-6 against 1e-10, tests/golden/sensitivity.json): the
+  blast front keeps producing states with |M| >= E that the recovery must
+  clamp.
+
+With SHASTA_REPORT_DIR set, the measured errors are written to
+full_size_report.json there.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1206_0919_gb300 import shasta as S
+from paper_1206_0919_gb300 import workloads as W
+from oracle import oracle as OR
+from gpu_util import oracle, rel_l1, require_gpu
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+REPORT = {}
+
+
+def report(key, value):
+    REPORT[key] = value
+    d = os.environ.get("SHASTA_REPORT_DIR")
+    if d:
+        with open(os.path.join(d, "full_size_report.json"), "w") as fh:
+            json.dump(REPORT, fh, indent=1, sort_keys=True)
+
+
+def totals_gap(got, ref):
+    """max over fields of |sum(got) - sum(ref)| / sum|ref|."""
+    out = []
+    for g, r in zip(got, ref):
+        out.append(abs(float(np.sum(g)) - float(np.sum(r))) / max(float(np.abs(r).sum()), 1e-300))
+    return out
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "sensitivity.json")
+
+
+def sensitivity():
+    with open(GOLDEN) as fh:
+        return json.load(fh)
+
+
+@pytest.fixture(scope="module")
+def config2():
+    require_gpu()
+    N = 200
+    P = OR.params((N, N, N))
+    O = oracle()
+    U0 = O.prim2cons(P, *W.hot_spots(N=N, seed=2, n_spots=30).as_list())
+    U75 = O.step(P, U0, 75)
+    e75 = O.recover(P, U75)["e"]
+    ref = O.step(P, U75, 125, step0=75)
+    return U0, e75, ref, O.recover(P, ref)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_config2_full_size_against_oracle(config2, precision):
+    U0, e75, ref, rp = config2
+    N = 200
+    with S.Solver((N, N, N), precision=precision) as s:  # autotune + graphs, as benched
+        s.set_conserved(U0)
+        s.step(75)
+        err75 = rel_l1(s.get_primitives()["e"], e75)
+        s.step(125)
+        got = s.get_conserved()
+        prim = s.get_primitives()
+    err200 = rel_l1(prim["e"], rp["e"])
+    gaps = totals_gap(got, ref)
+    drift = [abs(float(np.sum(g)) - float(np.sum(u))) / float(np.abs(u).sum())
+             for g, u in zip((got[0], got[4]), (U0[0], U0[4]))]
+    envelope = sensitivity()["hot_spots_200_input_rounding"]["200"]
+    report(f"config2_{precision}", {"rel_l1_e_75": err75, "rel_l1_e_200": err200,
+                                    "fp64_input_rounding_envelope_200": envelope,
+                                    "totals_gap_vs_oracle_200": gaps,
+                                    "drift_E_R_vs_initial_200": drift})
+    assert err75 <= 1e-4, err75
+    assert err200 <= 10 * envelope, (err200, envelope)
+    assert max(gaps) <= 1e-5, gaps
+    assert max(drift) <= 1e-5, drift
+
+
+def test_config3_sampled_events_against_oracle():
+    require_gpu()
+    evs = W.batch_events(n_events=64, seed=3)
+    total = sum(ev["N"] ** 3 for ev in evs)
+    smallest = sorted(range(len(evs)), key=lambda i: evs[i]["N"])[:3]
+    inputs = {}
+    with S.Batch(total + 64 * len(evs), precision="mixed", max_events=len(evs)) as b:
+        ids = []
+        for i, ev in enumerate(evs):
+            pr = W.event_prims(ev).as_list()
+            if i in smallest:
+                inputs[i] = pr
+            ids.append(b.add_primitives((ev["N"],) * 3, pr))
+        b.step(100)
+        got = {i: (b.get_primitives(ids[i]), b.get_conserved(ids[i])) for i in smallest}
+    O = oracle()
+    errs = {}
+    for i in smallest:
+        N = evs[i]["N"]
+        P = OR.params((N, N, N))
+        ref = O.step(P, O.prim2cons(P, *inputs[i]), 100)
+        rp = O.recover(P, ref)
+        errs[i] = (rel_l1(got[i][0]["e"], rp["e"]), max(totals_gap(got[i][1], ref)))
+    report("config3_sampled_mixed", {f"event{i}_N{evs[i]['N']}": {"rel_l1_e": e, "totals_gap": t}
+                                     for i, (e, t) in errs.items()})
+    for i, (e, t) in errs.items():
+        assert e <= 1e-4 and t <= 1e-5, (i, e, t)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_config5_blast(precision):
+    require_gpu()
+    # 512^3, 500 steps: conservation of E and R in the closed box
+    N = 512
+    pr = W.blast(N=N, radius=40.0)
+    with S.Solver((N, N, N), precision=precision) as s:
+        s.set_primitives(*pr.as_list())
+        t0 = s.totals()
+        s.step(500)
+        t1 = s.totals()
+        clamps = s.counters()
+    del pr
+    drift = [abs(t1[k] - t0[k]) / abs(t0[k]) for k in (0, 4)]
+    # the same setup at 128^3 against the oracle at the same clamp margin
+    n = 128
+    small = W.blast(N=n, radius=10.0)
+    O = oracle()
+    P = OR.params((n, n, n), delta=1e-6)
+    U0 = O.prim2cons(P, *small.as_list())
+    U50 = O.step(P, U0, 50)
+    e50 = O.recover(P, U50)["e"]
+    ref = O.step(P, U50, 75, step0=50)
+    rp = O.recover(P, ref)
+    with S.Solver((n, n, n), precision=precision, delta=1e-6) as s:
+        s.set_conserved(U0)
+        s.step(50)
+        err50 = rel_l1(s.get_primitives()["e"], e50)
+        s.step(75)
+        prim = s.get_primitives()
+        got = s.get_conserved()
+    err125 = rel_l1(prim["e"], rp["e"])
+    gaps = totals_gap(got, ref)
+    envelope = sensitivity()["blast_128_delta_1e-6_vs_1e-10"]["125"]
+    report(f"config5_{precision}", {"drift_E_R_512": drift, "clamped_recoveries_512": clamps,
+                                    "rel_l1_e_128_50": err50, "rel_l1_e_128_125": err125,
+                                    "fp64_clamp_margin_envelope_125": envelope,
+                                    "totals_gap_128_125": gaps})
+    assert max(drift) <= 1e-5, drift
+    assert max(gaps) <= 1e-5, gaps
+    assert err50 <= 1e-4, err50
+    assert err125 <= 3 * envelope, (err125, envelope)
