@@ -288,10 +288,12 @@ bool admit(shasta_server* s) {
   return true;
 }
 
-// One round: admit the events copied in during the previous round, take
-// finished ones out, enqueue the next steps, and while they run copy the
-// next queue heads in (first come first served, while slots, pool room and
-// input staging allow), then wait for the steps.
+// One round: take finished events out, enqueue the next steps of the
+// resident ones, and while those run copy the next queue heads in (first
+// come first served, while slots, pool room and input staging allow) and
+// admit them into the batch (stream-ordered after the steps, so they join
+// from the next round on; the admission's synchronisation also waits for
+// the steps).
 void worker_main(shasta_server* s) {
   cudaSetDevice(s->o.device);
   double tp[7] = {};  // [4] (copy out) is kept by the deliverer
@@ -314,8 +316,6 @@ void worker_main(shasta_server* s) {
         continue;
       }
     }
-    if (!admit(s)) break;
-    lap(1);
     if (!harvest(s)) break;
     lap(2);
     if (!s->resident.empty()) {
@@ -373,6 +373,8 @@ void worker_main(shasta_server* s) {
     }
     if (!ok) break;
     lap(0);
+    if (!admit(s)) break;
+    lap(1);
     if (shasta_batch_sync(s->batch) != SHASTA_OK) {
       stop_all(s, batch_msg(s, "sync"));
       break;
