@@ -223,6 +223,15 @@ SweepParams sweep_params(shasta_ctx* c, int axis, int from, int variant, long lo
   P.clamp_count = c->d_count;
   P.range_len = range < 1 ? 1 : range;
   P.variant = variant;
+  if (c->o.precision == SHASTA_FP64) {
+    // one thread per line segment: about 1024 threads per SM, segments of
+    // at least 16 cells (each re-reads a 6-cell halo per side)
+    const long long want = (long long)c->sm_count * 1024;
+    long long nseg = (want + P.plane - 1) / P.plane;
+    const long long cap = P.n / 16 > 1 ? P.n / 16 : 1;
+    nseg = nseg < 1 ? 1 : (nseg > cap ? cap : nseg);
+    P.range_len = (P.n + nseg - 1) / nseg;
+  }
   if (c->o.precision != SHASTA_FP64) {
     // at most one wave of resident warps loops over the ranges
     const long long total = work_positions(c, axis);

@@ -271,17 +271,26 @@ __device__ __forceinline__ void load_ext(const SweepParams& P, long long base, l
 
 // T: storage and transport type.  R: recovery type.  FAST: float limiter
 // with sign-bit arithmetic (same values as the branchy form).
+// One thread streams positions [s0, s1) of one line (the segment seg of
+// line t; P.range_len cells per segment, whole lines when it is 0 or >= n),
+// starting 2 NG positions early: the pipeline windows then hold exactly what
+// a whole-line pass holds at s0, so segments give the same bits.
 template <class T, class R, int EOS, int AXIS, bool FAST>
 __global__ void __launch_bounds__(128) sweep_kernel(SweepParams P) {
   constexpr int FPAR = 1 + AXIS;
   constexpr int FT1 = AXIS == 0 ? 2 : 1;
   constexpr int FT2 = AXIS == 2 ? 2 : 3;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= P.plane) return;
+  const int n = P.n;
+  const int L = P.range_len > 0 && P.range_len < n ? (int)P.range_len : n;
+  const int nseg = (n + L - 1) / L;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= P.plane * nseg) return;
+  const long long t = tid % P.plane;
+  const int s0 = (int)(tid / P.plane) * L;
+  const int s1 = s0 + L < n ? s0 + L : n;
   const long long b = t % P.nb;
   const long long c = t / P.nb;
   const long long base = b * P.sb + c * P.sc;
-  const int n = P.n;
   const bool frozen = P.bc == BC_FROZEN;
 
   const T tau_h = T(P.tau_h), tau_f = T(P.tau_f);
@@ -316,9 +325,9 @@ __global__ void __launch_bounds__(128) sweep_kernel(SweepParams P) {
   }
 
   T nxt[NF];
-  load_ext<T, AXIS>(P, base, t, -NG - NG, nxt);
+  load_ext<T, AXIS>(P, base, t, s0 - 2 * NG, nxt);
 
-  for (int q = -2 * NG; q <= n + 2 * NG - 1; ++q) {
+  for (int q = s0 - 2 * NG; q <= s1 + 2 * NG - 1; ++q) {
     // ---- stage 0: ingest U^n_q, prefetch q+1, recover (w, p)^n_q
 #pragma unroll
     for (int s = 0; s < 7; ++s)
@@ -326,7 +335,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(SweepParams P) {
       for (int k = 0; k < NF; ++k) u[s][k] = u[s + 1][k];
 #pragma unroll
     for (int k = 0; k < NF; ++k) u[7][k] = nxt[k];
-    if (q + 1 <= n + 2 * NG - 1) load_ext<T, AXIS>(P, base, t, q + 1, nxt);
+    if (q + 1 <= s1 + 2 * NG - 1) load_ext<T, AXIS>(P, base, t, q + 1, nxt);
     wn[0] = wn[1];
     wn[1] = wn[2];
     pn[0] = pn[1];
@@ -335,7 +344,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(SweepParams P) {
       R w, p;
       const unsigned c0 = recover_wp<R, EOS, AXIS>(R(u[7][0]), R(u[7][1]), R(u[7][2]),
                                                    R(u[7][3]), omd, B, ec, w, p);
-      nclamp += (q >= 0 && q < n) ? c0 : 0u;
+      nclamp += (q >= s0 && q < s1) ? c0 : 0u;
       wn[2] = T(w);
       pn[2] = T(p);
     }
@@ -376,7 +385,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(SweepParams P) {
       R w, p;
       const unsigned c3 =
           recover_wp<R, EOS, AXIS>(R(hs[0]), R(hs[1]), R(hs[2]), R(hs[3]), omd, B, ec, w, p);
-      nclamp += (jh >= 0 && jh < n) ? c3 : 0u;
+      nclamp += (jh >= s0 && jh < s1) ? c3 : 0u;
       wh[2] = T(w);
       ph[2] = T(p);
     }
@@ -404,7 +413,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(SweepParams P) {
       af[k] = an;
     }
     const int jo = q - 2 * NG;
-    if (jo >= 0) {
+    if (jo >= s0) {
       long long i = base + (long long)jo * P.stride;
       static_cast<T*>(P.out[0])[i] = outv[0];
       static_cast<T*>(P.out[FPAR])[i] = outv[1];

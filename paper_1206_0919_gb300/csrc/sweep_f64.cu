@@ -8,7 +8,9 @@ namespace shasta {
 template <int EOS, int AXIS>
 static cudaError_t go(const SweepParams& P, cudaStream_t s) {
   const int threads = 128;
-  long long blocks = (P.plane + threads - 1) / threads;
+  const int L = P.range_len > 0 && P.range_len < P.n ? (int)P.range_len : P.n;
+  const long long work = P.plane * ((P.n + L - 1) / L);
+  long long blocks = (work + threads - 1) / threads;
   sweep_kernel<double, double, EOS, AXIS, false><<<(unsigned)blocks, threads, 0, s>>>(P);
   return cudaGetLastError();
 }
