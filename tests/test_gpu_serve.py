@@ -144,3 +144,20 @@ def test_queue_full_and_bad_events():
         assert srv.poll(tg)["steps"] == 4
         st = srv.stats()
         assert st["failed"] == 1 and st["finished"] == 1
+
+
+def test_drain_times_out_then_completes():
+    """A bounded wait that runs out returns ETIMEOUT and leaves the server
+    working: the event still finishes and a later drain succeeds."""
+    require_gpu()
+    shape = (96, 96, 96)
+    with S.Server(1 << 30) as srv:
+        t = srv.submit(shape, prims_of(shape, 7, "ideal"), 400)
+        with pytest.raises(S.ShastaError) as ei:
+            srv.drain(1e-4)
+        assert ei.value.status == S.ETIMEOUT
+        r = srv.poll(t)  # almost surely still running (about 100 rounds of steps)
+        if r is None:
+            srv.drain(120.0)
+            r = srv.poll(t)
+        assert r["steps"] == 400
