@@ -488,9 +488,11 @@ def run_batch(args):
         dist.barrier()
     torch.cuda.synchronize()
     t_wall0 = time.time()
+    torch.cuda.nvtx.range_push("timed_steps")  # profilers can filter on this range
     ev0.record(stream)
     b.step(args.steps)
     ev1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
