@@ -278,3 +278,28 @@ def test_autotune_keeps_state():
     for a, b in zip(before, after):
         assert np.array_equal(a, b)
     assert all(v in (0, 1) and r >= 1 for v, r in tune)
+
+
+@pytest.mark.parametrize("gamma,bound", [(10.0, 1e-4), (100.0, 5e-3)])
+def test_mixed_recovery_at_high_gamma(gamma, bound):
+    """A shock tube boosted along x to Lorentz factor gamma (periodic box),
+    40 steps.  MIXED evaluates the recovery's E^2 - |M|^2 without
+    cancellation and ends closer to the FP64 oracle than FP32; both stay
+    within `bound` (relative L1 error of e).  The FP32 state itself limits
+    both: E - |M| carries only about eps * 2 gamma^2 relative precision."""
+    shape = (128, 16, 16)
+    v = np.sqrt(1.0 - 1.0 / gamma ** 2)
+    p0 = W.shock_tube(*shape, e_l=1.0, e_r=0.1, n_l=1.0, n_r=0.1)
+    prims = [p0.e, np.full_like(p0.e, v), p0.vy, p0.vz, p0.n]
+    O = oracle()
+    P = OR.params(shape, bc=OR.BC_PERIODIC)
+    U0 = O.prim2cons(P, *prims)
+    ref = O.recover(P, O.step(P, U0, 40))
+    err = {}
+    for precision in ("fp32", "mixed"):
+        with S.Solver(shape, precision=precision, bc="periodic") as s:
+            s.set_conserved(U0)
+            s.step(40)
+            err[precision] = rel_l1(s.get_primitives()["e"], ref["e"])
+    assert err["mixed"] < err["fp32"], err
+    assert err["mixed"] <= bound and err["fp32"] <= bound, err
