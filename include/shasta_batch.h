@@ -3,8 +3,8 @@
  *
  * A batch keeps the state of many events in one device pool and advances
  * every resident event with one launch per sweep axis over a work list of
- * (event, line group, segment) items, instead of one launch per event and
- * sweep.  The paper weighs the size of a kernel's working set against the
+ * its events (work units: whole line groups, or equal ranges of positions
+ * that may cut lines), instead of one launch per event and sweep.  The paper weighs the size of a kernel's working set against the
  * cost of orchestrating many kernel calls from the host (Sec. 3.1.2) and
  * enqueues the sweeps of one grid from a host loop (Sec. 3.1.3); here the
  * work of all events of a sweep shares a launch, and six steps of launches

@@ -45,7 +45,7 @@ struct Event {
 struct LaunchRec {
   int axis = 0, eos = 0, nlist = 0;
   size_t idx_off = 0, pre_off = 0, gpre_off = 0;  // event indices, position / group prefixes
-  long long items = 0;   // positions
+  long long items = 0;   // (line group, position) pairs
   long long groups = 0;  // line groups
 };
 

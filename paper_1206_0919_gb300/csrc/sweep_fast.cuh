@@ -157,8 +157,8 @@ __device__ __forceinline__ void negate_par(f2& A, f2& B) {
   if (AXIS == 2) B.y = -B.y;
 }
 
-// Geometry and coefficients of the event a work item belongs to, held in
-// registers (one event of a batch).
+// Geometry and coefficients of the event a piece of work belongs to, held
+// in registers (one event of a batch).
 struct ItemGeo {
   long long off;     // first cell of the event in the state arrays
   long long stride;  // cell stride along the line
@@ -170,7 +170,7 @@ struct ItemGeo {
   unsigned long long* clamp;
 };
 
-// Item geometry accessors.  GeoP reads the launch parameters at each use
+// Geometry accessors.  GeoP reads the launch parameters at each use
 // (the single event of a launch: the values stay constant-bank operands);
 // GeoR returns the registers of an ItemGeo.
 struct GeoP {
@@ -275,9 +275,7 @@ __device__ __forceinline__ void copy_cell(const SweepParams& P, const Geo& G, fl
 
 // Velocity along the sweep and pressure of one cell, FP32 (MIXED: D in
 // double-float).  mx, my, mz are the momenta, m1 the one along the sweep.
-// For an unclamped cell with the ideal gas this evaluates exactly the
-// expressions of the packed routine below, so a cell's result never depends
-// on the cell it is paired with.  Returns 1 if |M| was clamped or E <= 0.
+// Returns 1 if |M| was clamped or E <= 0.
 template <int EOS, bool MIXED>
 __device__ __forceinline__ unsigned rec32(float E, float mx, float my, float mz, float m1,
                                           float omd, float B, float ec, float& w, float& p) {
@@ -343,7 +341,7 @@ __device__ __forceinline__ unsigned rec32(float E, float mx, float my, float mz,
 // The two recoveries of a streaming step (halves lo: U^n of the newest
 // cell, hi: U^(n+1/2) four cells back): E, the three momenta and the
 // momentum along the sweep.  cnt counts the lo cell when in_seg (a cell of
-// the item's own segment) and it was clamped or vacuum.
+// the piece's own positions) and it was clamped or vacuum.
 template <int EOS, bool MIXED>
 __device__ __forceinline__ void rec2(f2 E, f2 mx, f2 my, f2 mz, f2 mpar, float omd, float B,
                                      float ec, f2& w, f2& p, unsigned& cnt, bool in_seg) {
@@ -493,7 +491,7 @@ using bc_ = std::integral_constant<bool, V>;
 // ------------------------------------------------------------- kernel ----
 //
 // Pipeline (q = newest loaded position; lag 7):
-//   U^n_q read; (w, p)^n_q and (w, p)^h_{q-4} recovered together (packed)
+//   U^n_q read; (w, p)^n_q and (w, p)^h_{q-4} recovered (two scalar chains)
 //   half-step pass of (E, M) with newest cell q      -> U^h_{q-3}
 //   full-step pass of (E, M, R) with newest cell q-4 -> U^{n+1}_{q-7}
 
@@ -876,13 +874,13 @@ __device__ __forceinline__ void sweep_items(const SweepParams& P, const BatchLis
   }
 }
 
-// One event: the launch's items are those of P.
+// One event: the launch's work is that of P.
 template <int EOS, int AXIS, bool MIXED, int WARPS, int RING, int DIST, int MINB>
 __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParams P) {
   sweep_items<EOS, AXIS, MIXED, WARPS, RING, DIST, false>(P, BatchList{});
 }
 
-// A batch: the items of every event of the work list L, all swept along
+// A batch: the work of every event of the work list L, all swept along
 // AXIS; P supplies the batch's state arrays, eta and 1 - delta.
 template <int EOS, int AXIS, bool MIXED, int WARPS, int RING, int DIST, int MINB>
 __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_batch_kernel(SweepParams P, BatchList L) {
