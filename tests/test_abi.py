@@ -78,3 +78,58 @@ def test_batch_and_server_without_gpu_fail_cleanly(lib):
     with pytest.raises(S.ShastaError) as ei:
         S.Batch(1 << 20, precision="fp64")
     assert ei.value.status == S.EINVAL
+
+
+def test_null_handles_are_rejected(lib):
+    """Every entry point given a NULL handle or NULL output returns an error
+    status (or its documented sentinel) without touching the device."""
+    import ctypes as C
+    null = None
+    i64 = (C.c_int64 * 16)()
+    dbl = (C.c_double * 16)()
+    ints = (C.c_int * 8)()
+    ptrs5 = (C.c_void_p * 5)()
+    ptrs6 = (C.c_void_p * 6)()
+    # single event
+    assert lib.shasta_destroy(null) == S.OK
+    assert lib.shasta_set_conserved(null, None, None, None, None, None, 0) == S.EINVAL
+    assert lib.shasta_set_primitives(null, None, None, None, None, None, 0) == S.EINVAL
+    assert lib.shasta_step(null, 1) == S.EINVAL
+    assert lib.shasta_sweep(null, 0) == S.EINVAL
+    assert lib.shasta_sync(null) == S.EINVAL
+    assert lib.shasta_autotune(null) == S.EINVAL
+    assert lib.shasta_get_tuning(null, ints) == S.EINVAL
+    assert lib.shasta_get_conserved(null, None, None, None, None, None, 0) == S.EINVAL
+    assert lib.shasta_get_primitives(null, None, None, None, None, None, None, 0) == S.EINVAL
+    assert lib.shasta_totals(null, dbl) == S.EINVAL
+    assert lib.shasta_steps_done(null) == -1
+    assert lib.shasta_set_step_counter(null, 0) == S.EINVAL
+    assert lib.shasta_counters(null, i64) == S.EINVAL
+    assert lib.shasta_stream(null) is None
+    assert lib.shasta_create(None, 1.0, 0.4, None, None, None) == S.EINVAL
+    # batches
+    assert lib.shasta_batch_destroy(null) == S.OK
+    assert lib.shasta_batch_create(None, None) == S.EINVAL
+    assert lib.shasta_batch_add(null, None, 1.0, 0.4, None, ptrs5, 0, 0, None) == S.EINVAL
+    assert lib.shasta_batch_remove(null, 0) == S.EINVAL
+    assert lib.shasta_batch_step(null, 1) == S.EINVAL
+    assert lib.shasta_batch_sync(null) == S.EINVAL
+    assert lib.shasta_batch_autotune(null) == S.EINVAL
+    assert lib.shasta_batch_get_conserved(null, 0, ptrs5, 0) == S.EINVAL
+    assert lib.shasta_batch_get_primitives(null, 0, ptrs6, 0) == S.EINVAL
+    assert lib.shasta_batch_totals(null, 0, dbl) == S.EINVAL
+    assert lib.shasta_batch_steps_done(null, 0) == -1
+    assert lib.shasta_batch_counters(null, 0, i64) == S.EINVAL
+    assert lib.shasta_batch_info(null, i64) == S.EINVAL
+    assert lib.shasta_batch_stream(null) is None
+    assert lib.shasta_batch_last_error(null) is not None
+    # serving
+    assert lib.shasta_server_destroy(null) == S.OK
+    assert lib.shasta_server_create(None, None) == S.EINVAL
+    assert lib.shasta_submit(null, None, None) == S.EINVAL
+    assert lib.shasta_poll(null, 1, None) == S.EINVAL
+    assert lib.shasta_server_drain(null, 0.0) == S.EINVAL
+    assert lib.shasta_server_stats(null, dbl) == S.EINVAL
+    assert lib.shasta_server_clock(null) == 0.0
+    assert lib.shasta_server_last_error(null) is not None
+    assert lib.shasta_last_error(null) is not None
