@@ -101,6 +101,11 @@ shasta_status shasta_batch_totals(shasta_batch* b, int id, double out[5]);
 /* Steps the event has taken since it was added, or -1 if id is unknown. */
 int64_t shasta_batch_steps_done(const shasta_batch* b, int id);
 
+/* Sets an event's step counter (the phase of the axis permutation is this
+ * mod 6), e.g. to resume an event saved with shasta_batch_get_conserved and
+ * shasta_batch_steps_done.  Errors: ENOTFOUND, EINVAL (negative). */
+shasta_status shasta_batch_set_step_counter(shasta_batch* b, int id, int64_t steps);
+
 /* Clamp / vacuum recoveries of the event since it was added (as
  * shasta_counters).  Synchronous. */
 shasta_status shasta_batch_counters(shasta_batch* b, int id, int64_t out[1]);

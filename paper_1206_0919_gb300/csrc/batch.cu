@@ -893,6 +893,21 @@ int64_t shasta_batch_steps_done(const shasta_batch* b, int id) {
   return b->ev[id].steps;
 }
 
+shasta_status shasta_batch_set_step_counter(shasta_batch* b, int id, int64_t steps) {
+  Event* e = find(b, id);
+  if (!e) return b ? fail(b, SHASTA_ENOTFOUND, "unknown event id") : SHASTA_EINVAL;
+  if (steps < 0) return fail(b, SHASTA_EINVAL, "negative step counter");
+  if (steps != e->steps) {
+    // the work lists follow every event's phase; the enqueued steps were
+    // planned with the old one
+    DeviceGuard dg(b->device);
+    CK(cudaStreamSynchronize(b->stream), "sync");
+    e->steps = steps;
+    b->plan_valid = false;
+  }
+  return SHASTA_OK;
+}
+
 shasta_status shasta_batch_counters(shasta_batch* b, int id, int64_t out[1]) {
   Event* e = find(b, id);
   if (!e) return b ? fail(b, SHASTA_ENOTFOUND, "unknown event id") : SHASTA_EINVAL;

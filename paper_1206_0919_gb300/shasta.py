@@ -120,6 +120,7 @@ SIGNATURES = {
     "shasta_batch_get_primitives": (C.c_int, [_vp, C.c_int, C.POINTER(_vp), C.c_int]),
     "shasta_batch_totals": (C.c_int, [_vp, C.c_int, _dp]),
     "shasta_batch_steps_done": (C.c_int64, [_vp, C.c_int]),
+    "shasta_batch_set_step_counter": (C.c_int, [_vp, C.c_int, C.c_int64]),
     "shasta_batch_counters": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int64)]),
     "shasta_batch_info": (C.c_int, [_vp, C.POINTER(C.c_int64)]),
     "shasta_batch_stream": (_vp, [_vp]),
@@ -457,6 +458,9 @@ class Batch:
 
     def steps_done(self, eid):
         return int(lib().shasta_batch_steps_done(self._h, eid))
+
+    def set_step_counter(self, eid, steps):
+        _bcheck(lib().shasta_batch_set_step_counter(self._h, eid, int(steps)), self._h)
 
     def counters(self, eid):
         out = (C.c_int64 * 1)()

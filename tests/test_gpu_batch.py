@@ -185,3 +185,26 @@ def test_batch_device_arrays_and_empty_step():
         got = [o.cpu().numpy() for o in out]
     ref, _, _ = single(shape, "reflect", "ideal", pr, 5, "fp32")
     assert all(np.array_equal(g, r) for g, r in zip(got, ref))
+
+
+def test_batch_checkpoint_resume_bitwise():
+    """An event saved after 5 steps (conserved state + step counter) and
+    added again with its counter restored continues exactly as if it had
+    never left the batch, while another event keeps running."""
+    require_gpu()
+    shape, other = (32, 24, 20), (24, 24, 24)
+    pa, pb = prims_of(shape, 41, 0.1, "ideal"), prims_of(other, 42, 0.0, "ideal")
+    cap = 4 * (32 * 24 * 20 + 24 ** 3)
+    with S.Batch(cap, check_input=False) as b:  # a saved state is taken as it is
+        ia, ib = b.add_primitives(shape, pa), b.add_primitives(other, pb)
+        b.step(5)
+        saved, k = b.get_conserved(ia), b.steps_done(ia)
+        b.remove(ia)
+        b.step(2)  # the other event runs on meanwhile
+        ia2 = b.add_conserved(shape, saved)
+        b.set_step_counter(ia2, k)
+        b.step(9)
+        got = b.get_conserved(ia2)
+        assert b.steps_done(ia2) == 14
+    ref, _, _ = single(shape, "reflect", "ideal", pa, 14, "fp32")
+    assert all(np.array_equal(g, r) for g, r in zip(got, ref))
