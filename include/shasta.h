@@ -220,9 +220,9 @@ int64_t shasta_steps_done(const shasta_ctx* ctx);
  * shasta_get_conserved + shasta_steps_done.  Errors: EINVAL (negative). */
 shasta_status shasta_set_step_counter(shasta_ctx* ctx, int64_t steps);
 
-/* Device counters since the state was last set: out[0] = cell recoveries in
- * which |M| was clamped or E <= 0 (the solver's vacuum/clamp reading).
- * Synchronous. */
+/* Device counters since the state was last set: out[0] = recoveries of the
+ * level-n state (each cell once per sweep) in which |M| was clamped or
+ * E <= 0 (the solver's vacuum/clamp reading).  Synchronous. */
 shasta_status shasta_counters(shasta_ctx* ctx, int64_t out[1]);
 
 /* The context's stream (cudaStream_t as void*). */

@@ -383,9 +383,8 @@ __global__ void __launch_bounds__(128) sweep_kernel(SweepParams P) {
     ph[1] = ph[2];
     {
       R w, p;
-      const unsigned c3 =
-          recover_wp<R, EOS, AXIS>(R(hs[0]), R(hs[1]), R(hs[2]), R(hs[3]), omd, B, ec, w, p);
-      nclamp += (jh >= s0 && jh < s1) ? c3 : 0u;
+      // (the counter counts level-n recoveries only, as the FP32 kernels)
+      recover_wp<R, EOS, AXIS>(R(hs[0]), R(hs[1]), R(hs[2]), R(hs[3]), omd, B, ec, w, p);
       wh[2] = T(w);
       ph[2] = T(p);
     }

@@ -642,8 +642,10 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, i
       const f2 mz = pk(hi_of(uB), hi_of(HB));
       const f2 mpar = AXIS == 0 ? mx : (AXIS == 1 ? my : mz);
       f2 w2, p2;
+      // count each cell of the piece once (lanes past the last line only
+      // repeat it)
       rec2<EOS, MIXED>(E, mx, my, mz, mpar, omd, B, ec, w2, p2, nclamp,
-                       (unsigned)(q - s0) < (unsigned)(s1 - s0));
+                       valid && (unsigned)(q - s0) < (unsigned)(s1 - s0));
       float pl, phi, pwl, pwh;
       up(w2, wn0, wh0);
       up(p2, pl, phi);

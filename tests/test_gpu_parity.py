@@ -230,12 +230,18 @@ def test_clamp_counter():
             s.set_conserved(U0)
             s.step(2)
             assert s.counters() == 0
-        bad = [u.copy() for u in U0]
-        bad[1][3, 3, 3] = 1.5 * bad[0][3, 3, 3]  # |M| > E in one cell
+    # one |M| > E cell in the last line of a sweep whose last line group is
+    # mostly padding lanes (35 lines): counted exactly once per sweep
+    shape = (16, 7, 5)
+    pr = W.hot_spots(shape=shape, seed=9, n_spots=3, sigma=(2.0, 3.0), background=0.1)
+    U0 = oracle().prim2cons(OR.params(shape), *pr.as_list())
+    bad = [u.copy() for u in U0]
+    bad[1][4, 6, 9] = 1.5 * bad[0][4, 6, 9]
+    for precision in ("fp64", "fp32", "mixed"):
         with S.Solver(shape, precision=precision, check_input=False) as s:
             s.set_conserved(bad)
             s.sweep(0)
-            assert s.counters() >= 1
+            assert s.counters() == 1, precision
 
 
 @pytest.mark.parametrize("precision", ["fp32", "mixed", "fp64"])
