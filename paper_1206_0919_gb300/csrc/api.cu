@@ -231,6 +231,7 @@ SweepParams sweep_params(shasta_ctx* c, int axis, int from, int variant, long lo
     const long long cap = P.n / 16 > 1 ? P.n / 16 : 1;
     nseg = nseg < 1 ? 1 : (nseg > cap ? cap : nseg);
     P.range_len = (P.n + nseg - 1) / nseg;
+    if (c->force_range > 0) P.range_len = c->force_range;  // environment override
   }
   if (c->o.precision != SHASTA_FP64) {
     // at most one wave of resident warps loops over the ranges

@@ -246,8 +246,9 @@ def test_clamp_counter():
 
 @pytest.mark.parametrize("precision", ["fp32", "mixed", "fp64"])
 def test_graphs_and_launch_choices_bitwise(monkeypatch, precision):
-    """CUDA-graph replay, the autotuner and every forced launch choice
-    (segments per line, register variant) give bitwise identical states."""
+    """CUDA-graph replay, the autotuner and every forced launch choice (work
+    range length, register variant; FP64: line segment length) give bitwise
+    identical states."""
     shape = (72, 56, 48)
     pr = W.hot_spots(shape=shape, seed=21, n_spots=6, sigma=(2.0, 4.0), radial_flow=0.1)
     O = oracle()
@@ -261,11 +262,11 @@ def test_graphs_and_launch_choices_bitwise(monkeypatch, precision):
 
     ref = run(autotune=False, use_graphs=False)
     outs = [run(autotune=True, use_graphs=True)]
-    if precision != "fp64":
-        for rng, var in ((100000, 0), (37, 1), (24, 0), (5, 1)):
-            monkeypatch.setenv("SHASTA_RANGE", str(rng))
-            monkeypatch.setenv("SHASTA_VARIANT", str(var))
-            outs.append(run(autotune=False, use_graphs=True))
+    # forced work ranges (FP64: segment lengths, whole lines for 100000)
+    for rng, var in ((100000, 0), (37, 1), (24, 0), (5, 1)):
+        monkeypatch.setenv("SHASTA_RANGE", str(rng))
+        monkeypatch.setenv("SHASTA_VARIANT", str(var))
+        outs.append(run(autotune=False, use_graphs=True))
     for out in outs:
         for a, b in zip(ref, out):
             assert np.array_equal(a, b)
