@@ -29,6 +29,7 @@ thread_local std::string g_server_create_error;
 constexpr int kMaxStaged = 4;             // events copied in ahead of admission
 constexpr long long kPoolAlign = 32;      // cells, as the batch pool
 constexpr long long kStateBytes = 40;     // device bytes of state per cell (two buffers)
+constexpr size_t kBounceHalf = 16u << 20; // bytes per half of a pinned bounce buffer
 
 enum JobState { J_WAIT, J_STAGED, J_RESIDENT, J_OUT, J_DONE, J_FAILED };
 
@@ -48,6 +49,59 @@ struct Job {
 
 using JobP = std::shared_ptr<Job>;
 
+// Two pinned host buffers used in turn to bring results back to the
+// callers' (pageable) arrays: the DMA into one half overlaps the CPU copy out
+// of the other.  A device-to-pageable copy would be staged by the driver on
+// the calling thread and measurably delays the worker thread's CUDA calls
+// (the rounds' gaps between step launches); a copy into pinned memory is
+// plain asynchronous DMA.
+struct Bounce {
+  char* buf = nullptr;  // 2 * kBounceHalf bytes
+  cudaEvent_t done[2] = {};
+};
+
+cudaError_t bounce_init(Bounce& b) {
+  cudaError_t e = cudaMallocHost((void**)&b.buf, 2 * kBounceHalf);
+  if (e != cudaSuccess) {
+    b.buf = nullptr;
+    return e;
+  }
+  for (int h = 0; h < 2 && e == cudaSuccess; ++h)
+    e = cudaEventCreateWithFlags(&b.done[h], cudaEventDisableTiming);
+  return e;
+}
+
+void bounce_free(Bounce& b) {
+  for (int h = 0; h < 2; ++h)
+    if (b.done[h]) cudaEventDestroy(b.done[h]);
+  if (b.buf) cudaFreeHost(b.buf);
+  b = Bounce();
+}
+
+struct Piece {
+  char* dst;
+  const char* src;
+  size_t len;
+};
+
+// Device -> host (pageable) for a list of pieces of at most kBounceHalf
+// bytes, through `st`; returns when every piece is in place.
+cudaError_t bounce_d2h(Bounce& b, const std::vector<Piece>& pcs, cudaStream_t st) {
+  auto issue = [&](size_t k) {
+    const int h = (int)(k & 1);
+    cudaError_t e = cudaMemcpyAsync(b.buf + h * kBounceHalf, pcs[k].src, pcs[k].len,
+                                    cudaMemcpyDeviceToHost, st);
+    return e == cudaSuccess ? cudaEventRecord(b.done[h], st) : e;
+  };
+  cudaError_t e = pcs.empty() ? cudaSuccess : issue(0);
+  for (size_t k = 0; k < pcs.size() && e == cudaSuccess; ++k) {
+    if (k + 1 < pcs.size()) e = issue(k + 1);  // its half was emptied in step k - 1
+    if (e == cudaSuccess) e = cudaEventSynchronize(b.done[k & 1]);
+    if (e == cudaSuccess) memcpy(pcs[k].dst, b.buf + (k & 1) * kBounceHalf, pcs[k].len);
+  }
+  return e;
+}
+
 }  // namespace
 
 struct shasta_server {
@@ -59,6 +113,7 @@ struct shasta_server {
   char* in_base = nullptr;
   char* out_base = nullptr;
   RangeAlloc in_arena{256}, out_arena{256};
+  Bounce bounce;  // the deliverer's
   long long pool_cells = 0;
   std::chrono::steady_clock::time_point t0;
   std::mutex mu;  // guards the queue, the job table, out_arena, deliver and the counters
@@ -160,19 +215,20 @@ void deliverer_main(shasta_server* s) {
       s->deliver.pop_front();
     }
     const double t0 = now(s);
-    const double* base = (const double*)(s->out_base + j->out_off);
+    const char* base = s->out_base + j->out_off;
     const size_t bytes = (size_t)j->ncell * sizeof(double);
-    int k = 0;
-    cudaError_t e = cudaSuccess;
-    for (int i = 0; i < 6 && e == cudaSuccess; ++i)
-      if (j->ev.out_prims[i])
-        e = cudaMemcpyAsync(j->ev.out_prims[i], base + (size_t)(k++) * j->ncell, bytes,
-                            cudaMemcpyDeviceToHost, s->copy_out);
-    for (int i = 0; i < 5 && e == cudaSuccess; ++i)
-      if (j->ev.out_cons[i])
-        e = cudaMemcpyAsync(j->ev.out_cons[i], base + (size_t)(k++) * j->ncell, bytes,
-                            cudaMemcpyDeviceToHost, s->copy_out);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->copy_out);
+    std::vector<Piece> pcs;
+    size_t k = 0;
+    auto field = [&](double* dst) {
+      for (size_t off = 0; off < bytes; off += kBounceHalf)
+        pcs.push_back(Piece{(char*)dst + off, base + k * bytes + off, std::min(kBounceHalf, bytes - off)});
+      ++k;
+    };
+    for (int i = 0; i < 6; ++i)
+      if (j->ev.out_prims[i]) field(j->ev.out_prims[i]);
+    for (int i = 0; i < 5; ++i)
+      if (j->ev.out_cons[i]) field(j->ev.out_cons[i]);
+    cudaError_t e = bounce_d2h(s->bounce, pcs, s->copy_out);
     {
       std::lock_guard<std::mutex> lk(s->mu);
       s->out_arena.release(j->out_off, j->out_bytes);
@@ -400,6 +456,7 @@ void release(shasta_server* s) {
   for (const JobP& j : s->staged)
     if (j->in_ready) cudaEventDestroy(j->in_ready);
   cudaFree(s->staging);
+  bounce_free(s->bounce);
   if (s->compute) cudaStreamDestroy(s->compute);
   if (s->copy) cudaStreamDestroy(s->copy);
   if (s->copy_out) cudaStreamDestroy(s->copy_out);
@@ -467,6 +524,9 @@ shasta_status shasta_server_create(const shasta_server_opts* o, shasta_server** 
   if (ce != cudaSuccess)
     return bail(ce == cudaErrorMemoryAllocation ? SHASTA_ENOMEM : SHASTA_ECUDA,
                 std::string("staging: ") + cudaGetErrorString(ce));
+  ce = bounce_init(s->bounce);
+  if (ce != cudaSuccess)
+    return bail(SHASTA_ENOMEM, std::string("pinned host buffers: ") + cudaGetErrorString(ce));
   s->in_base = (char*)s->staging;
   s->out_base = (char*)s->staging + s->in_cap;
   s->in_arena.reset(s->in_cap);
@@ -480,7 +540,7 @@ shasta_status shasta_server_create(const shasta_server_opts* o, shasta_server** 
   bo.device = opts.device;
   bo.check_input = 1;
   bo.autotune = 0;  // the set of events changes every few steps: the model picks
-  bo.use_graphs = 1;
+  bo.use_graphs = 0;  // and a graph would be captured again for almost every round
   bo.max_events = opts.max_resident;
   bo.capacity_cells = std::min<long long>(cells, 1LL << 31);
   shasta_status st = shasta_batch_create(&bo, &s->batch);

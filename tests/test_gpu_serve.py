@@ -54,15 +54,17 @@ def test_results_same_alone_and_in_the_mix(precision):
     require_gpu()
     alone = [run_alone(sh, eos, k, seed, precision) for sh, eos, k, seed in MIX]
     # the mix: at most three resident at once, so that later events join a
-    # batch that is already running
+    # batch that is already running (inputs made first: the submissions
+    # follow each other closely)
+    inputs = [prims_of(sh, seed, eos) for sh, eos, k, seed in MIX]
     with S.Server(1 << 30, precision=precision, max_resident=3, steps_per_round=1) as srv:
-        tickets = [srv.submit(sh, prims_of(sh, seed, eos), k, eos=eos, cons_out=True)
-                   for sh, eos, k, seed in MIX]
+        tickets = [srv.submit(sh, pr, k, eos=eos, cons_out=True)
+                   for (sh, eos, k, seed), pr in zip(MIX, inputs)]
         srv.drain(120.0)
         mixed = [srv.poll(t) for t in tickets]
         st = srv.stats()
     assert st["finished"] == len(MIX) and st["failed"] == 0
-    assert st["peak_resident"] >= 2  # events really shared the batch
+    assert st["peak_resident"] >= 2, st  # events really shared the batch
     for (sh, eos, k, seed), a, m in zip(MIX, alone, mixed):
         assert a["steps"] == m["steps"] == k
         for key in ("e", "vx", "vy", "vz", "n", "p"):
