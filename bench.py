@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--mode", choices=["full", "kernels"], default="full",
                     help="kernels: only warmup + K steps (for profiler captures)")
-    ap.add_argument("--workload", choices=["single", "batch64", "serve", "tube64", "blast512"],
+    ap.add_argument("--workload", choices=["single", "batch64", "serve", "tube64", "blast512", "ball200"],
                     default="single",
                     help="single: one 200^3 hot-spot event (the headline); batch64: 64 events "
                          "of sizes from {48,64,96,128,160}^3 advanced as one batch; serve: a "
@@ -760,6 +760,70 @@ def run_fixed(args):
     return 0
 
 
+def run_ball(args):
+    """ball200: the expanding ball of Sec. 4 (radius 2 fm at dx = 0.2 fm = 10
+    cells, constant e = 1 in a box at 1e-6) on 200^3 for 200 steps (16 fm/c),
+    with the fused sweeps and without antidiffusion (the with / without
+    anti-flux comparison), the time of every step recorded."""
+    import torch
+
+    from paper_1206_0919_gb300 import shasta as S
+    from paper_1206_0919_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    N, steps = 200, 200
+    prims = W.ball(N=N)
+    ncell = N ** 3
+    cfg = {"workload": "expanding_ball_200^3", "grid": [N] * 3, "steps": steps, "radius": 10,
+           "e_in": 1.0, "e_out": 1e-6, "lambda": 0.4, "eta": 0.125, "bc": "reflect",
+           "eos": "ideal p=e/3", "data": "synthetic"}
+    legs = (("fp32", "fused", steps), ("fp32", "no_antiflux", steps), ("mixed", "fused", steps),
+            ("fp64", "fused", 20), ("fp64", "no_antiflux", 20))
+    out = {}
+    for prec, scheme, k in legs:
+        with S.Solver((N, N, N), precision=prec, scheme=scheme, stream=stream.cuda_stream,
+                      device=local) as s:
+            s.set_primitives(*prims.as_list())
+            t0 = s.totals()
+            s.autotune()
+            secs = timed_steps(s, stream, k)  # six-step graphs
+            t1 = s.totals()
+            clamps = s.counters()
+            # the expansion again, one step at a time, each timed
+            s.set_primitives(*prims.as_list())
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(k + 1)]
+            ev[0].record(stream)
+            for i in range(k):
+                s.step(1)
+                ev[i + 1].record(stream)
+            torch.cuda.synchronize()
+            per = [ev[i].elapsed_time(ev[i + 1]) for i in range(k)]
+            tenth = max(1, k // 10)
+            out[f"{prec}_{scheme}"] = {
+                "value": ncell * k / secs, "unit": UNIT, "steps": k, "ms_per_step": secs * 1e3 / k,
+                "ms_per_step_first_tenth": sum(per[:tenth]) / tenth,
+                "ms_per_step_last_tenth": sum(per[-tenth:]) / tenth,
+                "ms_per_step_min_max": [min(per), max(per)],
+                "drift_E": abs(t1[0] - t0[0]) / abs(t0[0]),
+                "drift_R": abs(t1[4] - t0[4]) / abs(t0[4]), "clamps": clamps}
+    main = out["fp32_fused"]
+    if rank == 0:
+        line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": 1,
+                "steps": main["steps"], "warmup": 0, "ms_per_step": main["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic", "config": cfg, "legs": out,
+                "antiflux_cost": {p: out[f"{p}_fused"]["ms_per_step"] / out[f"{p}_no_antiflux"]["ms_per_step"]
+                                  for p in ("fp32", "fp64")},
+                "cpu_baseline": None,
+                "roofline": {"bound": "hbm", "achieved": ncell * 120 / (main["ms_per_step"] / 1e3) / 1e9,
+                             "peak": measured_peak()[0], "unit": "GB/s"}}
+        line["roofline"]["frac"] = line["roofline"]["achieved"] / line["roofline"]["peak"]
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -772,6 +836,8 @@ def main():
         return run_serve(args)
     if args.workload in ("tube64", "blast512"):
         return run_fixed(args)
+    if args.workload == "ball200":
+        return run_ball(args)
     return run_ours(args)
 
 

@@ -91,19 +91,28 @@ typedef struct shasta_opts {
                       results do not depend on the choice */
   int use_graphs;  /* nonzero: runs of six steps starting at phase 0 replay one
                       captured CUDA graph of 18 sweeps */
+  int scheme;      /* SHASTA_SCHEME_*: how a sweep is computed (below) */
 } shasta_opts;
+
+/* Sweep schemes.  FUSED (the default) is the method of Sec. 3 in one fused
+ * kernel per sweep.  NO_ANTIFLUX leaves antidiffusion and flux limiter out
+ * (A = 0 in Eq. shasta-n: the transport alone, the same result as eta = 0);
+ * with FP32 it runs kernels without that stage, so that its cost can be
+ * measured (the with / without anti-flux comparison of Sec. 4); FP64 and
+ * MIXED run the fused kernels with eta = 0 (same result, same cost). */
+enum { SHASTA_SCHEME_FUSED = 0, SHASTA_SCHEME_NO_ANTIFLUX = 1 };
 
 typedef struct shasta_ctx shasta_ctx;
 
 /* Fills *o with the defaults: FP32, eta = 1/8, delta = 0, stream NULL,
- * device 0, check_input 1, autotune 1, use_graphs 1. */
+ * device 0, check_input 1, autotune 1, use_graphs 1, scheme FUSED. */
 void shasta_default_opts(shasta_opts* o);
 
 /* Creates a solver for one event.  dx is the cell size, lambda = dt/dx the
  * CFL number of Sec. 3 (0 < lambda <= 0.5); the time step is dt = lambda*dx.
  * eos may be NULL (ideal gas), o may be NULL (defaults).  Allocates two
  * copies of the five conserved fields on the device (double buffering,
- * Sec. 3.1.3).  Errors: EINVAL (sizes < 1, bad lambda/eta/eos, NULL out,
+ * Sec. 3.1.3).  Errors: EINVAL (sizes < 1, bad lambda/eta/eos/scheme, NULL out,
  * FP32 / MIXED grids of 2^32 cells or more), ENOMEM, ECUDA.  On error *out is NULL and shasta_last_error(NULL) holds
  * the message. */
 shasta_status shasta_create(const shasta_grid* g, double dx, double lambda,

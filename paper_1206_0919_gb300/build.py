@@ -36,6 +36,7 @@ UNITS = [
     ("server.cu", EXACT),
     ("sweep_f64.cu", EXACT),
     ("sweep_f32.cu", FAST),
+    ("sweep_f32_noaf.cu", FAST),
     ("sweep_mixed.cu", FAST),
     ("batch_f32.cu", FAST),
     ("batch_mixed.cu", FAST),

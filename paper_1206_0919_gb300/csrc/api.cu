@@ -216,7 +216,9 @@ SweepParams sweep_params(shasta_ctx* c, int axis, int from, int variant, long lo
   P.tau_f = c->lambda;
   P.htau_h = 0.5 * P.tau_h;
   P.htau_f = 0.5 * P.tau_f;
-  P.eta = c->o.eta;
+  // NO_ANTIFLUX: the FP32 kernels leave the stage out; the others compute
+  // it with eta = 0, which gives A = 0
+  P.eta = c->o.scheme == SHASTA_SCHEME_NO_ANTIFLUX ? 0.0 : c->o.eta;
   P.omd = 1.0 - c->o.delta;
   P.bag_B = c->eos.B;
   P.bag_ec = c->eos.e_c;
@@ -259,6 +261,8 @@ void launch_choice(const shasta_ctx* c, int axis, int& variant, long long& range
 cudaError_t launch_params(shasta_ctx* c, int axis, const SweepParams& P) {
   if (c->o.precision == SHASTA_FP64) return launch_sweep_f64(P, axis, c->eos.kind, c->stream);
   if (c->o.precision == SHASTA_MIXED) return launch_sweep_mixed(P, axis, c->eos.kind, c->stream);
+  if (c->o.scheme == SHASTA_SCHEME_NO_ANTIFLUX)
+    return launch_sweep_f32_noaf(P, axis, c->eos.kind, c->stream);
   return launch_sweep_f32(P, axis, c->eos.kind, c->stream);
 }
 
@@ -371,6 +375,7 @@ void shasta_default_opts(shasta_opts* o) {
   o->check_input = 1;
   o->autotune = 1;
   o->use_graphs = 1;
+  o->scheme = SHASTA_SCHEME_FUSED;
 }
 
 shasta_status shasta_create(const shasta_grid* g, double dx, double lambda, const shasta_eos* eos,
@@ -399,6 +404,8 @@ shasta_status shasta_create(const shasta_grid* g, double dx, double lambda, cons
     return fail(nullptr, SHASTA_EINVAL, "FP32 / MIXED grids hold fewer than 2^32 cells");
   if (!(opts.eta >= 0.0 && opts.eta <= 0.5)) return fail(nullptr, SHASTA_EINVAL, "need 0 <= eta <= 0.5");
   if (!(opts.delta >= 0.0 && opts.delta < 0.5)) return fail(nullptr, SHASTA_EINVAL, "need 0 <= delta < 0.5");
+  if (opts.scheme != SHASTA_SCHEME_FUSED && opts.scheme != SHASTA_SCHEME_NO_ANTIFLUX)
+    return fail(nullptr, SHASTA_EINVAL, "unknown scheme");
   if (opts.delta == 0.0) opts.delta = opts.precision == SHASTA_FP64 ? 1e-10 : 1e-6;
   shasta_eos e;
   if (eos)
@@ -483,7 +490,9 @@ shasta_status shasta_create(const shasta_grid* g, double dx, double lambda, cons
   err = cudaMallocHost((void**)&c->h_small, 16 * sizeof(double));
   if (err != cudaSuccess) return bail(err, "cudaMallocHost");
   if (opts.precision != SHASTA_FP64) {
-    err = opts.precision == SHASTA_MIXED ? prepare_sweep_mixed(c->occ) : prepare_sweep_f32(c->occ);
+    err = opts.precision == SHASTA_MIXED                 ? prepare_sweep_mixed(c->occ)
+          : opts.scheme == SHASTA_SCHEME_NO_ANTIFLUX ? prepare_sweep_f32_noaf(c->occ)
+                                                     : prepare_sweep_f32(c->occ);
     if (err != cudaSuccess) return bail(err, "prepare sweep kernels");
     c->wpb = opts.precision == SHASTA_MIXED ? sweep_warps_per_block_mixed() : sweep_warps_per_block_f32();
   }

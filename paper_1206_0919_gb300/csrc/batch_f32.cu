@@ -5,7 +5,7 @@
 namespace shasta {
 
 cudaError_t prepare_batch_f32(int occupancy[2][3][2]) {
-  return launch::prepare<false, true>(occupancy);
+  return launch::prepare<false, launch::BATCH>(occupancy);
 }
 
 cudaError_t launch_batch_f32(const SweepParams& P, const BatchList& L, int axis, int eos,

@@ -5,7 +5,7 @@
 namespace shasta {
 
 cudaError_t prepare_batch_mixed(int occupancy[2][3][2]) {
-  return launch::prepare<true, true>(occupancy);
+  return launch::prepare<true, launch::BATCH>(occupancy);
 }
 
 cudaError_t launch_batch_mixed(const SweepParams& P, const BatchList& L, int axis, int eos,

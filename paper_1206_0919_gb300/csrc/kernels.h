@@ -20,6 +20,10 @@ cudaError_t launch_sweep_mixed(const SweepParams& P, int axis, int eos, cudaStre
 cudaError_t prepare_sweep_f32(int occupancy[2][3][2]);
 cudaError_t prepare_sweep_mixed(int occupancy[2][3][2]);
 int sweep_warps_per_block_f32();
+// FP32 sweeps without the antidiffusion stage (sweep_f32_noaf.cu), same
+// launch parameters and occupancy layout as the fused FP32 sweeps.
+cudaError_t prepare_sweep_f32_noaf(int occupancy[2][3][2]);
+cudaError_t launch_sweep_f32_noaf(const SweepParams& P, int axis, int eos, cudaStream_t s);
 int sweep_warps_per_block_mixed();
 // Batched FP32 / MIXED sweeps (one launch over the work list L, all along
 // `axis`); prepare_* as above for the batched kernels.

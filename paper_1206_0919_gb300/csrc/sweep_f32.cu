@@ -4,7 +4,7 @@
 namespace shasta {
 
 cudaError_t prepare_sweep_f32(int occupancy[2][3][2]) {
-  return launch::prepare<false, false>(occupancy);
+  return launch::prepare<false, launch::SINGLE>(occupancy);
 }
 
 cudaError_t launch_sweep_f32(const SweepParams& P, int axis, int eos, cudaStream_t s) {

@@ -374,6 +374,8 @@ __device__ __forceinline__ float limit(float aph, float dhp, float dhm) {
 //   A_{k-3}     = limit(eta (Dh_{k-3} - D2_{k-3}/8), Dh_{k-2}, Dh_{k-4})    [phoenical + limiter]
 //   out_{k-3}   = (Uhat_{k-3} + A_{k-4}) - A_{k-3}                          [Eq. shasta-n]
 // Two-slot arrays are indexed by position parity; K is the parity of k.
+// With AF false the antidiffusion stage is left out (A = 0, the result of
+// eta = 0): out_{k-3} = Uhat_{k-3}, the transport alone.
 struct Line2 {
   f2 Up[2];  // U by parity
   f2 D[2];   // Delta
@@ -387,9 +389,17 @@ struct Line1 {
   float Up[2], D[2], DD[2], D2[2], Uh[2], Dh[2], A[2];
 };
 
-template <int K, bool SRC>
+template <int K, bool SRC, bool AF>
 __device__ __forceinline__ f2 step2(Line2& s, f2 u, f2 a2, f2 nb2, f2 c2, f2 src, f2 eta2, f2 m8) {
   constexpr int P0 = K & 1, P1 = (K + 1) & 1;  // parity of k (= k-2, k-4) and of k-1 (= k-3)
+  if constexpr (!AF) {
+    const f2 out = s.Uh[P1];                                     // Uhat_{k-3}
+    const f2 d = sub2(u, s.Up[P1]);
+    s.Uh[P1] = fma2(c2, s.Up[P1], fma2(a2, d, SRC ? fma2(nb2, s.D[P0], src) : mul2(nb2, s.D[P0])));
+    s.Up[P0] = u;
+    s.D[P1] = d;
+    return out;
+  }
   // values whose slots are overwritten below are consumed first
   const f2 aph = mul2(eta2, fma2(m8, s.D2[P1], s.Dh[P1]));        // A^ph_{k-3}
   const f2 t = add2(s.Uh[P1], s.A[P0]);                          // Uhat_{k-3} + A_{k-4}
@@ -410,9 +420,17 @@ __device__ __forceinline__ f2 step2(Line2& s, f2 u, f2 a2, f2 nb2, f2 c2, f2 src
   return sub2(t, A);
 }
 
-template <int K>
+template <int K, bool AF>
 __device__ __forceinline__ float step1(Line1& s, float u, float a, float nb, float c, float eta) {
   constexpr int P0 = K & 1, P1 = (K + 1) & 1;
+  if constexpr (!AF) {
+    const float out = s.Uh[P1];
+    const float d = u - s.Up[P1];
+    s.Uh[P1] = fmaf(c, s.Up[P1], fmaf(a, d, nb * s.D[P0]));
+    s.Up[P0] = u;
+    s.D[P1] = d;
+    return out;
+  }
   const float aph = eta * fmaf(-0.125f, s.D2[P1], s.Dh[P1]);
   const float qm = s.Dh[P0];
   const float t = s.Uh[P1] + s.A[P0];
@@ -498,7 +516,7 @@ using bc_ = std::integral_constant<bool, V>;
 // One piece of work: positions [s0, s1) of the 32 lines of line group g of
 // the event described by G (x path: s0 and, unless s1 = n, s1 on 8-cell
 // chunk boundaries).
-template <int EOS, int AXIS, bool MIXED, int RING, int DIST, class Geo>
+template <int EOS, int AXIS, bool MIXED, int RING, int DIST, bool AF, class Geo>
 __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, int g, int s0, int s1,
                                            float* wsm, int lane, unsigned& nclamp) {
   constexpr bool XP = AXIS == 0;
@@ -662,8 +680,8 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, i
       fn[P0] = fn0;
       wn1 = wn0;
       const f2 a2 = pk(a, a), nb2 = pk(nb, nb), c2 = pk(c, c);
-      HA = step2<K, true>(hA, uA, a2, nb2, c2, sA, eta2, m8c);
-      HB = step2<K, AXIS != 0>(hB, uB, a2, nb2, c2, sB, eta2, m8c);
+      HA = step2<K, true, AF>(hA, uA, a2, nb2, c2, sA, eta2, m8c);
+      HB = step2<K, AXIS != 0, AF>(hB, uB, a2, nb2, c2, sB, eta2, m8c);
       if (GH && frozen && (q - NG < 0 || q - NG >= n)) {
         // frozen ghost: the half-step state is the stored ghost value
         const float* s3 = XP ? x_slot((q - NG) >> 3) : wsm + ((q - NG - qs) & (RING - 1)) * YSLOT;
@@ -685,9 +703,9 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, i
       fh[P0] = fh0;
       wh1 = wh0;
       const f2 a2 = pk(a, a), nb2 = pk(nb, nb), c2 = pk(c, c);
-      oA = step2<K, true>(fA, vA, a2, nb2, c2, sA, eta2, m8c);
-      oB = step2<K, AXIS != 0>(fB, vB, a2, nb2, c2, sB, eta2, m8c);
-      oR = step1<K>(fR, vR, a, nb, c, eta);
+      oA = step2<K, true, AF>(fA, vA, a2, nb2, c2, sA, eta2, m8c);
+      oB = step2<K, AXIS != 0, AF>(fB, vB, a2, nb2, c2, sB, eta2, m8c);
+      oR = step1<K, AF>(fR, vR, a, nb, c, eta);
     }
     const int jo = q - LAG;
     if (XP) {
@@ -788,7 +806,7 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, i
 // piece per line group it touches, each with its own halo); on the x path
 // range boundaries are moved down to 8-cell chunk boundaries of their line.
 // A batch may instead take whole line groups as work units (range_len 0).
-template <int EOS, int AXIS, bool MIXED, int WARPS, int RING, int DIST, bool BATCH>
+template <int EOS, int AXIS, bool MIXED, int WARPS, int RING, int DIST, bool BATCH, bool AF = true>
 __device__ __forceinline__ void sweep_items(const SweepParams& P, const BatchList& L) {
   constexpr bool XP = AXIS == 0;
   extern __shared__ __align__(16) float smem[];
@@ -827,7 +845,7 @@ __device__ __forceinline__ void sweep_items(const SweepParams& P, const BatchLis
       for (int r = first; r < total; r += nwarps) {
         const int k = entry(r);
         const GeoR G{geo_of<AXIS>(L.ev[L.idx[k]])};
-        sweep_item<EOS, AXIS, MIXED, RING, DIST>(P, G, r - L.prefix[k], 0, G.n(), wsm, lane, nclamp);
+        sweep_item<EOS, AXIS, MIXED, RING, DIST, AF>(P, G, r - L.prefix[k], 0, G.n(), wsm, lane, nclamp);
         if (nclamp && G.g.clamp) atomicAdd(G.g.clamp, (unsigned long long)nclamp);
         nclamp = 0;
       }
@@ -847,7 +865,7 @@ __device__ __forceinline__ void sweep_items(const SweepParams& P, const BatchLis
         const int g = loc / n;
         const int s0 = loc - g * n;
         const int pe = min(end, x - s0 + n);  // the piece ends with the range or the line group
-        sweep_item<EOS, AXIS, MIXED, RING, DIST>(P, G, g, s0, s0 + (pe - x), wsm, lane, nclamp);
+        sweep_item<EOS, AXIS, MIXED, RING, DIST, AF>(P, G, g, s0, s0 + (pe - x), wsm, lane, nclamp);
         if (nclamp && G.g.clamp) atomicAdd(G.g.clamp, (unsigned long long)nclamp);
         nclamp = 0;
         x = pe;
@@ -868,7 +886,7 @@ __device__ __forceinline__ void sweep_items(const SweepParams& P, const BatchLis
         const int g = x / n;
         const int s0 = x - g * n;
         const int pe = min(end, x - s0 + n);
-        sweep_item<EOS, AXIS, MIXED, RING, DIST>(P, G, g, s0, s0 + (pe - x), wsm, lane, nclamp);
+        sweep_item<EOS, AXIS, MIXED, RING, DIST, AF>(P, G, g, s0, s0 + (pe - x), wsm, lane, nclamp);
         x = pe;
       }
     }
@@ -880,6 +898,13 @@ __device__ __forceinline__ void sweep_items(const SweepParams& P, const BatchLis
 template <int EOS, int AXIS, bool MIXED, int WARPS, int RING, int DIST, int MINB>
 __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParams P) {
   sweep_items<EOS, AXIS, MIXED, WARPS, RING, DIST, false>(P, BatchList{});
+}
+
+// One event without the antidiffusion stage (the transport alone): an
+// ablation measuring what antidiffusion and limiter cost.
+template <int EOS, int AXIS, int WARPS, int RING, int DIST, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB) sweep_noaf_kernel(SweepParams P) {
+  sweep_items<EOS, AXIS, false, WARPS, RING, DIST, false, false>(P, BatchList{});
 }
 
 // A batch: the work of every event of the work list L, all swept along

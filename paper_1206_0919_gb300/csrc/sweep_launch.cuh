@@ -10,10 +10,16 @@ namespace launch {
 
 constexpr int kWarps = 4, kRing = 8, kDist = 3;
 
-template <bool MIXED, bool BATCH, int EOS, int AXIS, int MINB>
+// Kernel families: one event, a batch, one event without antidiffusion
+// (FP32 only).
+enum Kind { SINGLE = 0, BATCH = 1, NOAF = 2 };
+
+template <bool MIXED, int KIND, int EOS, int AXIS, int MINB>
 void* kfun() {
-  if constexpr (BATCH)
+  if constexpr (KIND == BATCH)
     return (void*)fast::sweep_batch_kernel<EOS, AXIS, MIXED, kWarps, kRing, kDist, MINB>;
+  else if constexpr (KIND == NOAF)
+    return (void*)fast::sweep_noaf_kernel<EOS, AXIS, kWarps, kRing, kDist, MINB>;
   else
     return (void*)fast::sweep_fast_kernel<EOS, AXIS, MIXED, kWarps, kRing, kDist, MINB>;
 }
@@ -29,26 +35,26 @@ inline size_t smem_of(int axis) {
 
 // Kernel of (eos, axis, variant); variant 0: registers capped for 3 CTAs
 // (12 warps) per SM, 1: uncapped.
-template <bool MIXED, bool BATCH>
+template <bool MIXED, int KIND>
 void* kernel_of(int eos, int axis, int variant) {
   static void* const table[2][3][2] = {
-      {{kfun<MIXED, BATCH, EOS_IDEAL, 0, 3>(), kfun<MIXED, BATCH, EOS_IDEAL, 0, 1>()},
-       {kfun<MIXED, BATCH, EOS_IDEAL, 1, 3>(), kfun<MIXED, BATCH, EOS_IDEAL, 1, 1>()},
-       {kfun<MIXED, BATCH, EOS_IDEAL, 2, 3>(), kfun<MIXED, BATCH, EOS_IDEAL, 2, 1>()}},
-      {{kfun<MIXED, BATCH, EOS_BAG, 0, 3>(), kfun<MIXED, BATCH, EOS_BAG, 0, 1>()},
-       {kfun<MIXED, BATCH, EOS_BAG, 1, 3>(), kfun<MIXED, BATCH, EOS_BAG, 1, 1>()},
-       {kfun<MIXED, BATCH, EOS_BAG, 2, 3>(), kfun<MIXED, BATCH, EOS_BAG, 2, 1>()}}};
+      {{kfun<MIXED, KIND, EOS_IDEAL, 0, 3>(), kfun<MIXED, KIND, EOS_IDEAL, 0, 1>()},
+       {kfun<MIXED, KIND, EOS_IDEAL, 1, 3>(), kfun<MIXED, KIND, EOS_IDEAL, 1, 1>()},
+       {kfun<MIXED, KIND, EOS_IDEAL, 2, 3>(), kfun<MIXED, KIND, EOS_IDEAL, 2, 1>()}},
+      {{kfun<MIXED, KIND, EOS_BAG, 0, 3>(), kfun<MIXED, KIND, EOS_BAG, 0, 1>()},
+       {kfun<MIXED, KIND, EOS_BAG, 1, 3>(), kfun<MIXED, KIND, EOS_BAG, 1, 1>()},
+       {kfun<MIXED, KIND, EOS_BAG, 2, 3>(), kfun<MIXED, KIND, EOS_BAG, 2, 1>()}}};
   return table[eos][axis][variant];
 }
 
 // Sets the shared-memory attribute of every kernel of the table and reports
 // resident warps per SM [eos][axis][variant].
-template <bool MIXED, bool BATCH>
+template <bool MIXED, int KIND>
 cudaError_t prepare(int occupancy[2][3][2]) {
   for (int eos = 0; eos < 2; ++eos)
     for (int axis = 0; axis < 3; ++axis)
       for (int var = 0; var < 2; ++var) {
-        const void* k = kernel_of<MIXED, BATCH>(eos, axis, var);
+        const void* k = kernel_of<MIXED, KIND>(eos, axis, var);
         const size_t smem = smem_of(axis);
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -65,12 +71,12 @@ inline bool bad_choice(const SweepParams& P, int axis, int eos) {
          P.blocks < 1;
 }
 
-template <bool MIXED>
+template <bool MIXED, int KIND = SINGLE>
 cudaError_t launch_single(const SweepParams& P, int axis, int eos, cudaStream_t s) {
   if (P.plane <= 0) return cudaSuccess;
   if (bad_choice(P, axis, eos)) return cudaErrorInvalidValue;
   void* args[] = {const_cast<SweepParams*>(&P)};
-  return cudaLaunchKernel(kernel_of<MIXED, false>(eos, axis, P.variant), dim3((unsigned)P.blocks),
+  return cudaLaunchKernel(kernel_of<MIXED, KIND>(eos, axis, P.variant), dim3((unsigned)P.blocks),
                           dim3(kWarps * 32), args, smem_of(axis), s);
 }
 
@@ -80,7 +86,7 @@ cudaError_t launch_batch(const SweepParams& P, const BatchList& L, int axis, int
   if (L.nlist <= 0) return cudaSuccess;
   if (bad_choice(P, axis, eos) || !L.ev || !L.idx || !L.prefix) return cudaErrorInvalidValue;
   void* args[] = {const_cast<SweepParams*>(&P), const_cast<BatchList*>(&L)};
-  return cudaLaunchKernel(kernel_of<MIXED, true>(eos, axis, P.variant), dim3((unsigned)P.blocks),
+  return cudaLaunchKernel(kernel_of<MIXED, BATCH>(eos, axis, P.variant), dim3((unsigned)P.blocks),
                           dim3(kWarps * 32), args, smem_of(axis), s);
 }
 

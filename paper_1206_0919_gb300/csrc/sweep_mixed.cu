@@ -5,7 +5,7 @@
 namespace shasta {
 
 cudaError_t prepare_sweep_mixed(int occupancy[2][3][2]) {
-  return launch::prepare<true, false>(occupancy);
+  return launch::prepare<true, launch::SINGLE>(occupancy);
 }
 
 cudaError_t launch_sweep_mixed(const SweepParams& P, int axis, int eos, cudaStream_t s) {

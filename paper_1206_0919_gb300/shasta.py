@@ -46,7 +46,10 @@ class Eos(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("eta", C.c_double), ("delta", C.c_double),
                 ("stream", C.c_void_p), ("device", C.c_int), ("check_input", C.c_int),
-                ("autotune", C.c_int), ("use_graphs", C.c_int)]
+                ("autotune", C.c_int), ("use_graphs", C.c_int), ("scheme", C.c_int)]
+
+
+SCHEMES = {"fused": 0, "no_antiflux": 1}
 
 
 class BatchOpts(C.Structure):
@@ -243,7 +246,7 @@ class Solver:
 
     def __init__(self, shape, lam=0.4, dx=1.0, precision="fp32", bc="reflect", eos="ideal",
                  bag_B=0.1, bag_ec=0.5, eta=0.125, delta=0.0, stream=None, device=0,
-                 check_input=True, autotune=True, use_graphs=True):
+                 check_input=True, autotune=True, use_graphs=True, scheme="fused"):
         L = lib()
         nx, ny, nz = shape
         self.shape = (nx, ny, nz)
@@ -260,6 +263,7 @@ class Solver:
         o.check_input = 1 if check_input else 0
         o.autotune = 1 if autotune else 0
         o.use_graphs = 1 if use_graphs else 0
+        o.scheme = SCHEMES[scheme] if isinstance(scheme, str) else scheme
         h = _vp()
         _check(L.shasta_create(C.byref(g), dx, lam, C.byref(e), C.byref(o), C.byref(h)))
         self._h = h

@@ -119,6 +119,15 @@ def blast(N=512, radius=40.0, e_in=1e3, e_out=0.1, shape=None) -> Prims:
     return Prims(e, z0, z0.copy(), z0.copy(), n, dict(kind="blast", radius=radius))
 
 
+def ball(N=200, radius=10.0, e_in=1.0, e_out=1e-6, shape=None) -> Prims:
+    """Expanding ball of Sec. 4: a sphere of constant energy density at rest,
+    radius 2 fm at dx = 0.2 fm (10 cells), in a near-empty box (e_out, the
+    floor of the hot-spot states); n = e^(3/4)."""
+    pr = blast(N=N, radius=radius, e_in=e_in, e_out=e_out, shape=shape)
+    pr.meta = dict(kind="ball", radius=radius, e_in=e_in, e_out=e_out)
+    return pr
+
+
 def random_state(shape, seed=0, vmax=0.6, e_range=(0.05, 5.0)) -> Prims:
     """Smooth-free random primitives for stress tests: e log-uniform, |v| < vmax."""
     nx, ny, nz = shape
