@@ -763,8 +763,9 @@ def run_fixed(args):
 def run_ball(args):
     """ball200: the expanding ball of Sec. 4 (radius 2 fm at dx = 0.2 fm = 10
     cells, constant e = 1 in a box at 1e-6) on 200^3 for 200 steps (16 fm/c),
-    with the fused sweeps and without antidiffusion (the with / without
-    anti-flux comparison), the time of every step recorded."""
+    with the fused sweeps, without antidiffusion (the with / without
+    anti-flux comparison) and with the split decomposition of Sec. 3.1, the
+    time of every step recorded."""
     import torch
 
     from paper_1206_0919_gb300 import shasta as S
@@ -779,8 +780,8 @@ def run_ball(args):
     cfg = {"workload": "expanding_ball_200^3", "grid": [N] * 3, "steps": steps, "radius": 10,
            "e_in": 1.0, "e_out": 1e-6, "lambda": 0.4, "eta": 0.125, "bc": "reflect",
            "eos": "ideal p=e/3", "data": "synthetic"}
-    legs = (("fp32", "fused", steps), ("fp32", "no_antiflux", steps), ("mixed", "fused", steps),
-            ("fp64", "fused", 20), ("fp64", "no_antiflux", 20))
+    legs = (("fp32", "fused", steps), ("fp32", "no_antiflux", steps), ("fp32", "split", steps),
+            ("mixed", "fused", steps), ("fp64", "fused", 20), ("fp64", "no_antiflux", 20))
     out = {}
     for prec, scheme, k in legs:
         with S.Solver((N, N, N), precision=prec, scheme=scheme, stream=stream.cuda_stream,
@@ -816,6 +817,7 @@ def run_ball(args):
                 "data": "synthetic", "config": cfg, "legs": out,
                 "antiflux_cost": {p: out[f"{p}_fused"]["ms_per_step"] / out[f"{p}_no_antiflux"]["ms_per_step"]
                                   for p in ("fp32", "fp64")},
+                "split_vs_fused": out["fp32_split"]["ms_per_step"] / out["fp32_fused"]["ms_per_step"],
                 "cpu_baseline": None,
                 "roofline": {"bound": "hbm", "achieved": ncell * 120 / (main["ms_per_step"] / 1e3) / 1e9,
                              "peak": measured_peak()[0], "unit": "GB/s"}}

@@ -99,8 +99,13 @@ typedef struct shasta_opts {
  * (A = 0 in Eq. shasta-n: the transport alone, the same result as eta = 0);
  * with FP32 it runs kernels without that stage, so that its cost can be
  * measured (the with / without anti-flux comparison of Sec. 4); FP64 and
- * MIXED run the fused kernels with eta = 0 (same result, same cost). */
-enum { SHASTA_SCHEME_FUSED = 0, SHASTA_SCHEME_NO_ANTIFLUX = 1 };
+ * MIXED run the fused kernels with eta = 0 (same result, same cost).  SPLIT
+ * (FP32 only) is the alternative decomposition of Sec. 3.1: each pass as
+ * separate recovery, transport and antidiffusion kernels whose intermediate
+ * results go through device memory (about 50 extra bytes of device memory
+ * per cell); the method is the same, the rounding of a few differences is
+ * not. */
+enum { SHASTA_SCHEME_FUSED = 0, SHASTA_SCHEME_NO_ANTIFLUX = 1, SHASTA_SCHEME_SPLIT = 2 };
 
 typedef struct shasta_ctx shasta_ctx;
 

@@ -37,6 +37,7 @@ UNITS = [
     ("sweep_f64.cu", EXACT),
     ("sweep_f32.cu", FAST),
     ("sweep_f32_noaf.cu", FAST),
+    ("sweep_split.cu", FAST),
     ("sweep_mixed.cu", FAST),
     ("batch_f32.cu", FAST),
     ("batch_mixed.cu", FAST),

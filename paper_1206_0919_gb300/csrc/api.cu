@@ -34,6 +34,10 @@ struct shasta_ctx {
   int is32 = 1;
   size_t ncell = 0, esize = 4;
   void* state_mem = nullptr;  // both buffers
+  void* split_mem = nullptr;  // SPLIT scheme: the half-step state and the intermediates
+  float* split_q = nullptr;   // half-step state (quads, R)
+  float* split_r = nullptr;
+  float* split_scratch = nullptr;
   FieldView view[2] = {};     // where the fields of each buffer live
   float* quad[2] = {};        // FP32 / MIXED: (E, Mx, My, Mz) per cell
   float* rf[2] = {};          // FP32 / MIXED: R
@@ -263,6 +267,9 @@ cudaError_t launch_params(shasta_ctx* c, int axis, const SweepParams& P) {
   if (c->o.precision == SHASTA_MIXED) return launch_sweep_mixed(P, axis, c->eos.kind, c->stream);
   if (c->o.scheme == SHASTA_SCHEME_NO_ANTIFLUX)
     return launch_sweep_f32_noaf(P, axis, c->eos.kind, c->stream);
+  if (c->o.scheme == SHASTA_SCHEME_SPLIT)
+    return launch_sweep_split(P, axis, c->eos.kind, c->split_scratch, c->split_q, c->split_r,
+                              c->stream);
   return launch_sweep_f32(P, axis, c->eos.kind, c->stream);
 }
 
@@ -286,7 +293,7 @@ void drop_graph(shasta_ctx* c) {
 // (no line is cut) or of 1/4 .. 3 ranges per resident warp.  The choice
 // does not change results.
 shasta_status autotune(shasta_ctx* c) {
-  if (c->o.precision == SHASTA_FP64) {
+  if (c->o.precision == SHASTA_FP64 || c->o.scheme == SHASTA_SCHEME_SPLIT) {
     c->tuned = true;
     return SHASTA_OK;
   }
@@ -349,6 +356,7 @@ void release(shasta_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   cudaFree(c->state_mem);
+  cudaFree(c->split_mem);
   cudaFree(c->frozen);
   cudaFree(c->staging);
   cudaFree(c->partials);
@@ -404,8 +412,11 @@ shasta_status shasta_create(const shasta_grid* g, double dx, double lambda, cons
     return fail(nullptr, SHASTA_EINVAL, "FP32 / MIXED grids hold fewer than 2^32 cells");
   if (!(opts.eta >= 0.0 && opts.eta <= 0.5)) return fail(nullptr, SHASTA_EINVAL, "need 0 <= eta <= 0.5");
   if (!(opts.delta >= 0.0 && opts.delta < 0.5)) return fail(nullptr, SHASTA_EINVAL, "need 0 <= delta < 0.5");
-  if (opts.scheme != SHASTA_SCHEME_FUSED && opts.scheme != SHASTA_SCHEME_NO_ANTIFLUX)
+  if (opts.scheme != SHASTA_SCHEME_FUSED && opts.scheme != SHASTA_SCHEME_NO_ANTIFLUX &&
+      opts.scheme != SHASTA_SCHEME_SPLIT)
     return fail(nullptr, SHASTA_EINVAL, "unknown scheme");
+  if (opts.scheme == SHASTA_SCHEME_SPLIT && opts.precision != SHASTA_FP32)
+    return fail(nullptr, SHASTA_EINVAL, "the split scheme is FP32 only");
   if (opts.delta == 0.0) opts.delta = opts.precision == SHASTA_FP64 ? 1e-10 : 1e-6;
   shasta_eos e;
   if (eos)
@@ -474,6 +485,15 @@ shasta_status shasta_create(const shasta_grid* g, double dx, double lambda, cons
         c->view[b].s[k] = 1;
       }
     }
+  }
+  if (opts.scheme == SHASTA_SCHEME_SPLIT) {
+    const size_t half = ((c->ncell * 20 + 255) / 256) * 256;
+    const size_t scratch = split_scratch_floats(g->nx, g->ny, g->nz) * sizeof(float);
+    err = cudaMalloc(&c->split_mem, half + scratch);
+    if (err != cudaSuccess) return bail(err, "cudaMalloc split-scheme buffers");
+    c->split_q = (float*)c->split_mem;
+    c->split_r = c->split_q + 4 * c->ncell;
+    c->split_scratch = (float*)((char*)c->split_mem + half);
   }
   if (g->bc == SHASTA_BC_FROZEN) {
     err = cudaMalloc(&c->frozen, frozen_elems(g->nx, g->ny, g->nz) * c->esize);

@@ -24,6 +24,13 @@ int sweep_warps_per_block_f32();
 // launch parameters and occupancy layout as the fused FP32 sweeps.
 cudaError_t prepare_sweep_f32_noaf(int occupancy[2][3][2]);
 cudaError_t launch_sweep_f32_noaf(const SweepParams& P, int axis, int eos, cudaStream_t s);
+// The split scheme (sweep_split.cu): one FP32 sweep as recovery, transport
+// and antidiffusion kernels with intermediates in device memory.  half_q /
+// half_r hold the half-step state (the layout of P.qin / P.rin); scratch
+// holds split_scratch_floats(nx, ny, nz) floats.
+size_t split_scratch_floats(int nx, int ny, int nz);
+cudaError_t launch_sweep_split(const SweepParams& P, int axis, int eos, float* scratch,
+                               float* half_q, float* half_r, cudaStream_t s);
 int sweep_warps_per_block_mixed();
 // Batched FP32 / MIXED sweeps (one launch over the work list L, all along
 // `axis`); prepare_* as above for the batched kernels.

@@ -58,6 +58,16 @@ def test_create_without_gpu_fails_cleanly(lib):
     assert lib.shasta_version().startswith(b"shasta-gb300")
 
 
+def test_bad_scheme_is_rejected_before_any_device_call(lib):
+    """Unknown schemes and the split scheme outside FP32 are option errors
+    (EINVAL), found before the library looks for a device."""
+    for kw in ({"scheme": 7}, {"scheme": "split", "precision": "fp64"},
+               {"scheme": "split", "precision": "mixed"}):
+        with pytest.raises(S.ShastaError) as ei:
+            S.Solver((4, 4, 4), **kw)
+        assert ei.value.status == S.EINVAL, kw
+
+
 def test_batch_and_server_without_gpu_fail_cleanly(lib):
     try:
         import torch

@@ -1,6 +1,11 @@
 """The sweep schemes of include/shasta.h and the expanding ball, against the
 oracle (GPU).
 
+SPLIT is the alternative decomposition of Sec. 3.1 (separate recovery,
+transport and antidiffusion kernels, intermediates in device memory), FP32:
+the same method as the fused sweep, checked against the oracle with the
+FP32 bar and against the fused FP32 sweep.
+
 NO_ANTIFLUX leaves antidiffusion and flux limiter out of every pass: A = 0
 in the update of Sec. 3 (Eq. shasta-n), which is what the oracle computes
 with eta = 0 (A^ph = 0, so the limited flux is 0).  FP32 runs dedicated
@@ -111,4 +116,62 @@ def test_ball_against_oracle(scheme):
     got, prim, _ = run(shape, U0, 20, "fp32", scheme, delta=1e-6)
     assert rel_l1(prim["e"], rp6["e"]) <= 1e-4
     for g, r in zip(got, ref6):
+        assert abs(g.sum() - r.sum()) <= 1e-5 * np.abs(r).sum() + 1e-12
+
+
+@pytest.mark.parametrize("bc", [OR.BC_REFLECT, OR.BC_PERIODIC, OR.BC_FROZEN])
+@pytest.mark.parametrize("eos", [OR.EOS_IDEAL, OR.EOS_BAG])
+@pytest.mark.parametrize("shape", [(37, 21, 13), (40, 3, 2), (5, 33, 9), (1, 1, 1)])
+def test_split_against_oracle(shape, bc, eos):
+    """Ragged shapes, every boundary rule and both EoS, 7 steps: relative
+    L1 of e <= 1e-4 and totals within 1e-5 of the oracle; the first sweep's
+    clamp count equals the fused sweep's (same level-n state, same
+    recovery)."""
+    require_gpu()
+    P, U0 = state(shape, bc, eos, seed=5 * sum(shape) + bc + 3 * eos)
+    O = oracle()
+    ref = O.step(OR.params(shape, bc=bc, eos=eos, delta=1e-6), U0, 7)
+    rp = O.recover(OR.params(shape, bc=bc, eos=eos, delta=1e-6), ref)
+    got, prim, _ = run(shape, U0, 7, "fp32", "split", bc=bc, eos=eos)
+    assert rel_l1(prim["e"], rp["e"]) <= 1e-4
+    for g, r in zip(got, ref):
+        assert abs(g.sum() - r.sum()) <= 1e-5 * np.abs(r).sum() + 1e-12
+    counts = []
+    for scheme in ("split", "fused"):
+        with S.Solver(shape, precision="fp32", bc=BC_NAMES[bc], eos=EOS_NAMES[eos],
+                      scheme=scheme) as s:
+            s.set_conserved(U0)
+            s.sweep(0)
+            s.sync()
+            counts.append(s.counters())
+    assert counts[0] == counts[1]
+
+
+def test_split_close_to_fused_on_hot_spots():
+    """The two FP32 decompositions of the same method agree to rounding on
+    a hot-spot state (20 steps; they differ only in the order of a few
+    differences)."""
+    require_gpu()
+    shape = (48, 40, 36)
+    pr = W.hot_spots(shape=shape, seed=8, n_spots=6, sigma=(2.0, 4.0), radial_flow=0.1)
+    U0 = oracle().prim2cons(OR.params(shape), *pr.as_list())
+    _, pa, _ = run(shape, U0, 20, "fp32", "split")
+    _, pb, _ = run(shape, U0, 20, "fp32", "fused")
+    assert rel_l1(pa["e"], pb["e"]) <= 2e-5
+
+
+def test_ball_split_against_oracle():
+    """The 64^3 ball with the split scheme: FP32 bar against the oracle at
+    the FP32 clamp margin after 20 steps."""
+    require_gpu()
+    N = 64
+    shape = (N, N, N)
+    O = oracle()
+    P6 = OR.params(shape, delta=1e-6)
+    U0 = O.prim2cons(P6, *W.ball(N=N).as_list())
+    ref = O.step(P6, U0, 20)
+    rp = O.recover(P6, ref)
+    got, prim, _ = run(shape, U0, 20, "fp32", "split", delta=1e-6)
+    assert rel_l1(prim["e"], rp["e"]) <= 1e-4
+    for g, r in zip(got, ref):
         assert abs(g.sum() - r.sum()) <= 1e-5 * np.abs(r).sum() + 1e-12
