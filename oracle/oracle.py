@@ -21,7 +21,7 @@ SRC = os.path.join(HERE, "shasta_oracle.c")
 LIB = os.path.join(HERE, "liboracle.so")
 
 BC_REFLECT, BC_PERIODIC, BC_FROZEN = 0, 1, 2
-EOS_IDEAL, EOS_BAG = 0, 1
+EOS_IDEAL, EOS_BAG, EOS_TABLE = 0, 1, 2
 
 _lock = threading.Lock()
 
@@ -48,14 +48,22 @@ class Params(C.Structure):
         ("bc", C.c_int), ("eos", C.c_int),
         ("lam", C.c_double), ("eta", C.c_double),
         ("bag_B", C.c_double), ("bag_ec", C.c_double), ("delta", C.c_double),
+        ("table", C.POINTER(C.c_double)), ("table_n", C.c_int), ("table_de", C.c_double),
     ]
 
 
 def params(shape, lam=0.4, eta=0.125, bc=BC_REFLECT, eos=EOS_IDEAL, bag_B=0.1,
-           bag_ec=0.5, delta=1e-10) -> Params:
-    """shape = (nx, ny, nz)."""
+           bag_ec=0.5, delta=1e-10, table=None, table_de=0.0) -> Params:
+    """shape = (nx, ny, nz).  table: p at e = k * table_de (EOS_TABLE)."""
     nx, ny, nz = shape
-    return Params(nx, ny, nz, bc, eos, lam, eta, bag_B, bag_ec, delta)
+    P = Params(nx, ny, nz, bc, eos, lam, eta, bag_B, bag_ec, delta)
+    if table is not None:
+        t = np.ascontiguousarray(table, dtype=np.float64)
+        P._table = t  # keeps the array alive as long as the parameters
+        P.table = t.ctypes.data_as(C.POINTER(C.c_double))
+        P.table_n = t.size
+        P.table_de = table_de
+    return P
 
 
 def _p(a):
@@ -78,6 +86,8 @@ class Oracle:
         pp = C.POINTER(Params)
         L.or_eos_p.argtypes = [pp, C.c_double]
         L.or_eos_p.restype = C.c_double
+        L.or_fixed_point.argtypes = [pp, C.c_double, C.c_double, dp, dp]
+        L.or_fixed_point.restype = C.c_int
         L.or_prim2cons.argtypes = [pp, C.c_size_t] + [dp] * 10
         L.or_recover.argtypes = [pp, C.c_size_t] + [dp] * 11
         L.or_line.argtypes = [C.c_int, dp, dp, dp, C.c_double, C.c_double, dp]
@@ -106,6 +116,12 @@ class Oracle:
 
     def eos_p(self, P: Params, e: float) -> float:
         return self.L.or_eos_p(C.byref(P), e)
+
+    def fixed_point(self, P: Params, E: float, M: float):
+        """(e, p, iterations) of the tabulated recovery of one cell."""
+        e, p = C.c_double(), C.c_double()
+        it = self.L.or_fixed_point(C.byref(P), E, M, C.byref(e), C.byref(p))
+        return e.value, p.value, it
 
     def prim2cons(self, P: Params, e, vx, vy, vz, nb):
         e, vx, vy, vz, nb = map(_f64, (e, vx, vy, vz, nb))
@@ -171,7 +187,8 @@ def default() -> Oracle:
 
 def __getattr__(name):
     # module-level shortcuts: oracle.step(...), oracle.recover(...), ...
-    if name in ("set_threads", "get_threads", "axis", "eos_p", "prim2cons", "recover", "line",
+    if name in ("set_threads", "get_threads", "axis", "eos_p", "fixed_point", "prim2cons",
+                "recover", "line",
                 "frozen_capture", "sweep", "step", "totals"):
         return getattr(default(), name)
     raise AttributeError(name)

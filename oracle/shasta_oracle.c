@@ -56,11 +56,43 @@ int or_axis(long step, int sub) { return k_axis_table[3 * (int)(step % 6) + sub]
 
 /* ---------------------------------------------------------------- EoS ---- */
 
+/* Tabulated p(e) (Sec. 2: parametrised or tabulated EoS, interpolated):
+ * piecewise linear through (k de, table[k]); the last interval continues
+ * above the table, the first below it. */
+static double table_p(const or_params* P, double e) {
+  double x = e / P->table_de;
+  int k = (int)floor(x);
+  if (k < 0) k = 0;
+  if (k > P->table_n - 2) k = P->table_n - 2;
+  double f = x - (double)k;
+  return P->table[k] + f * (P->table[k + 1] - P->table[k]);
+}
+
 /* Sec. 2 closes the system with the ideal gas p = e/3.  The bag model
  * p = (e - 4B)/3 above e_c is an added workload, not from the paper. */
 double or_eos_p(const or_params* P, double e) {
+  if (P->eos == OR_EOS_TABLE) return table_p(P, e);
   if (P->eos == OR_EOS_BAG && e > P->bag_ec) return (e - 4.0 * P->bag_B) / 3.0;
   return e / 3.0;
+}
+
+/* Sec. 3: the paper finds the velocity by a fixed-point iteration so that a
+ * tabulated EoS can replace p = e/3: from M = (E + p) v and e = E - M v,
+ * |v| = M / (E + p(E - M |v|)).  Returns the number of iterations. */
+int or_fixed_point(const or_params* P, double E, double M, double* e_out, double* p_out) {
+  double v = M / (E + table_p(P, E));
+  int it = 0;
+  while (it < OR_FP_MAXIT) {
+    double vn = M / (E + table_p(P, E - M * v));
+    ++it;
+    double d = vn - v;
+    v = vn;
+    if (fabs(d) <= OR_FP_TOL) break;
+  }
+  double e = E - M * v;
+  *e_out = e;
+  *p_out = table_p(P, e);
+  return it;
 }
 
 /* Rest-frame energy density and pressure from E and |M| (already clamped).
@@ -69,6 +101,10 @@ double or_eos_p(const or_params* P, double e) {
  * E - |M| cancellation.  (The paper finds the same root by fixed-point
  * iteration, Sec. 3; the closed form is its exact limit.) */
 static void eos_solve(const or_params* P, double E, double M, double* e_out, double* p_out) {
+  if (P->eos == OR_EOS_TABLE) {
+    or_fixed_point(P, E, M, e_out, p_out);
+    return;
+  }
   double s = sqrt(4.0 * E * E - 3.0 * M * M);
   double pa = ((E - M) * (E + M)) / (s + E);
   double ea = 3.0 * pa;
@@ -387,6 +423,7 @@ int or_step(const or_params* P, double* E, double* Mx, double* My, double* Mz, d
             const double* frozen, long step0, long nsteps) {
   if (P->nx < 1 || P->ny < 1 || P->nz < 1) return 1;
   if (P->bc == OR_BC_FROZEN && !frozen) return 2;
+  if (P->eos == OR_EOS_TABLE && (!P->table || P->table_n < 2 || !(P->table_de > 0.0))) return 3;
   for (long s = step0; s < step0 + nsteps; ++s)
     for (int sub = 0; sub < 3; ++sub) or_sweep(P, or_axis(s, sub), E, Mx, My, Mz, R, frozen);
   return 0;

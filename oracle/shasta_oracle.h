@@ -23,7 +23,7 @@ extern "C" {
 #endif
 
 enum { OR_BC_REFLECT = 0, OR_BC_PERIODIC = 1, OR_BC_FROZEN = 2 };
-enum { OR_EOS_IDEAL = 0, OR_EOS_BAG = 1 };
+enum { OR_EOS_IDEAL = 0, OR_EOS_BAG = 1, OR_EOS_TABLE = 2 };
 
 typedef struct {
   int nx, ny, nz;
@@ -34,10 +34,26 @@ typedef struct {
   double bag_B;  /* bag constant B (bag EoS only) */
   double bag_ec; /* energy density where the bag EoS switches branch */
   double delta;  /* |M| is clamped to (1-delta)*E before recovery */
+  /* OR_EOS_TABLE: p at e_k = k * table_de, k = 0 .. table_n-1, linear in
+   * between and linearly extrapolated from the last interval above; the
+   * recovery then finds |v| by the fixed-point iteration of Sec. 3. */
+  const double* table;
+  int table_n;
+  double table_de;
 } or_params;
+
+/* Fixed-point iteration of the tabulated recovery: start v = M/(E + p(E)),
+ * iterate v <- M/(E + p(E - M v)) until |change| <= OR_FP_TOL or
+ * OR_FP_MAXIT iterations. */
+#define OR_FP_TOL 1e-14
+#define OR_FP_MAXIT 200
 
 /* Equation of state p(e). */
 double or_eos_p(const or_params* P, double e);
+
+/* Tabulated EoS: rest-frame e and p of a cell with energy E > 0 and |M| < E
+ * by the fixed-point iteration; returns the iterations taken. */
+int or_fixed_point(const or_params* P, double E, double M, double* e_out, double* p_out);
 
 /* Sec. 2, Eqs. (cf-density), (cf-momentum), (cf-energy): primitives -> conserved. */
 void or_prim2cons(const or_params* P, size_t n, const double* e, const double* vx,

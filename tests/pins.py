@@ -94,6 +94,129 @@ def pin_recover_fixed_point(O, seed=12):
             assert abs(e_root - (E - M * v)) <= 1e-12 * max(1.0, E), "fixed point e"
 
 
+# ------------------------------------------------- tabulated EoS (f2) ----
+#
+# Sec. 2 allows parametrised or tabulated equations of state, and Sec. 3
+# recovers the velocity by a fixed-point iteration precisely so that a table
+# can replace p = e/3.  The table holds p at e = k de, linear in between.
+
+IDEAL_DE = 0.01
+IDEAL_TABLE = np.arange(20001) * IDEAL_DE / 3.0  # p = e/3 for e <= 200
+
+
+def _soft(e, a=0.3):
+    """A smooth causal EoS for the pins: p = (e/3)(1 - exp(-e/a)), with
+    0 <= dp/de < 1/2 and p >= 0."""
+    return e / 3.0 * (1.0 - np.exp(-e / a))
+
+
+def pin_table_interpolation(O):
+    """p(e) of a table is the piecewise-linear interpolant: the samples at
+    the nodes, their mean at mid-intervals, the last interval continued
+    above the table."""
+    de = 0.05
+    e_nodes = np.arange(41) * de
+    tab = _soft(e_nodes)
+    P = OR.params((1, 1, 1), eos=OR.EOS_TABLE, table=tab, table_de=de)
+    for k in (0, 1, 17, 39, 40):
+        assert O.eos_p(P, e_nodes[k]) == tab[k], "node value"
+    for k in (0, 5, 39):
+        mid = O.eos_p(P, (k + 0.5) * de)
+        assert abs(mid - 0.5 * (tab[k] + tab[k + 1])) <= 1e-15, "mid-interval"
+    above = O.eos_p(P, 42 * de)
+    assert abs(above - (tab[40] + 2.0 * (tab[40] - tab[39]))) <= 1e-14, "extrapolation"
+
+
+def pin_table_ideal_matches_closed_form(O, seed=19):
+    """A table of p = e/3 (exact under linear interpolation) recovers what
+    the closed form of p = e/3 recovers, velocities up to 1 - 1e-4."""
+    rng = np.random.default_rng(seed)
+    n = 3000
+    e = 10.0 ** rng.uniform(-3, 2, n)
+    vmag = np.concatenate([rng.uniform(0, 0.95, n - 300), 1 - 10.0 ** rng.uniform(-4, -1.5, 300)])
+    d = rng.normal(size=(3, n))
+    d /= np.linalg.norm(d, axis=0)
+    v = d * vmag
+    nb = rng.uniform(0.1, 2.0, n)
+    Pi = OR.params((n, 1, 1))
+    Pt = OR.params((n, 1, 1), eos=OR.EOS_TABLE, table=IDEAL_TABLE, table_de=IDEAL_DE)
+    U = O.prim2cons(Pi, e, v[0], v[1], v[2], nb)
+    Ut = O.prim2cons(Pt, e, v[0], v[1], v[2], nb)
+    for a, b in zip(U, Ut):
+        assert np.all(np.abs(a - b) <= 1e-14 * np.abs(a) + 1e-300), "prim2cons through the table"
+    r = O.recover(Pt, U)
+    g2 = 1.0 / (1.0 - vmag ** 2)
+    # the iteration stops at |dv| <= 1e-14: e = E - M v carries M dv
+    tol = 1e-12 * g2 + 1e-13
+    assert np.all(np.abs(r["e"] - e) <= tol * e), "table recovery e"
+    for k, a in (("vx", 0), ("vy", 1), ("vz", 2)):
+        assert np.all(np.abs(r[k] - v[a]) <= tol), "table recovery " + k
+    assert np.all(np.abs(r["p"] - e / 3.0) <= tol * e), "table recovery p"
+
+
+def pin_table_roundtrip_soft(O, seed=20):
+    """prim -> cons -> prim through a nonlinear table returns e and v: the
+    fixed point solves M = (E + p) v, e = E - M v with the table's p."""
+    rng = np.random.default_rng(seed)
+    n = 2000
+    de = 0.005
+    tab = _soft(np.arange(20001) * de)
+    P = OR.params((n, 1, 1), eos=OR.EOS_TABLE, table=tab, table_de=de)
+    e = 10.0 ** rng.uniform(-2.5, 1.8, n)
+    vmag = rng.uniform(0, 0.97, n)
+    d = rng.normal(size=(3, n))
+    d /= np.linalg.norm(d, axis=0)
+    v = d * vmag
+    nb = rng.uniform(0.1, 2.0, n)
+    U = O.prim2cons(P, e, v[0], v[1], v[2], nb)
+    # E and M follow Sec. 2 with the interpolated p
+    x = e / de
+    k = np.minimum(np.floor(x).astype(int), tab.size - 2)
+    p = tab[k] + (x - k) * (tab[k + 1] - tab[k])
+    g2 = 1.0 / (1.0 - vmag ** 2)
+    assert np.all(np.abs(U[0] - ((e + p) * g2 - p)) <= 1e-13 * U[0]), "E of Sec. 2"
+    r = O.recover(P, U)
+    tol = 1e-12 * g2
+    assert np.all(np.abs(r["e"] - e) <= tol * e), "roundtrip e"
+    for kk, a in (("vx", 0), ("vy", 1), ("vz", 2)):
+        assert np.all(np.abs(r[kk] - v[a]) <= tol), "roundtrip " + kk
+    assert np.all(np.abs(r["n"] - nb) <= tol * nb), "roundtrip n"
+
+
+def pin_table_fixed_point_residual(O, seed=21):
+    """Each recovered cell satisfies the fixed-point equation
+    |v| = M / (E + p(E - M |v|)) and converges within the iteration cap."""
+    rng = np.random.default_rng(seed)
+    de = 0.005
+    tab = _soft(np.arange(20001) * de)
+    P = OR.params((1, 1, 1), eos=OR.EOS_TABLE, table=tab, table_de=de)
+    for _ in range(300):
+        E = 10.0 ** rng.uniform(-2, 1.9)
+        M = E * (1.0 - 10.0 ** rng.uniform(-5, 0))
+        e, p, it = O.fixed_point(P, E, M)
+        assert it < 200, "no convergence"
+        v = (E - e) / M if M > 0 else 0.0
+        x = e / de
+        k = min(int(math.floor(x)), tab.size - 2)
+        p_tab = tab[k] + (x - k) * (tab[k + 1] - tab[k])
+        assert p == p_tab, "p is the table's p at the recovered e"
+        assert abs(v - M / (E + p_tab)) <= 1e-13, "fixed-point residual"
+
+
+def pin_table_step_matches_ideal(O, seed=22):
+    """Full split steps with the p = e/3 table follow the closed-form ideal
+    gas (the table path through prim2cons, recovery and both passes)."""
+    shape = (14, 11, 9)
+    pr = W.random_state(shape, seed=seed, vmax=0.8)
+    Pi = OR.params(shape)
+    Pt = OR.params(shape, eos=OR.EOS_TABLE, table=IDEAL_TABLE, table_de=IDEAL_DE)
+    U0 = O.prim2cons(Pi, *pr.as_list())
+    a = O.step(Pi, U0, 4)
+    b = O.step(Pt, U0, 4)
+    for x, y in zip(a, b):
+        assert np.max(np.abs(x - y)) <= 1e-11 * np.max(np.abs(x)), "table step"
+
+
 def pin_bag_gap(O, seed=13):
     """Mixed-phase reading: in the EoS gap e = e_c and M = (E + p) v still holds."""
     rng = np.random.default_rng(seed)
@@ -423,6 +546,11 @@ def pin_frozen_edges_hold(O):
 FAST_PINS = [
     pin_recover_roundtrip,
     pin_recover_fixed_point,
+    pin_table_interpolation,
+    pin_table_ideal_matches_closed_form,
+    pin_table_roundtrip_soft,
+    pin_table_fixed_point_residual,
+    pin_table_step_matches_ideal,
     pin_bag_gap,
     pin_vacuum_and_clamp,
     pin_uniform_rest_bitwise,

@@ -44,6 +44,12 @@ MUTANTS = [
     ("energy definition", "E[i] = w - p;", "E[i] = w + p;"),
     ("frozen ghost side", "long edge = b + (side == 0 ? 0 : (long)(n - 1) * st);",
      "long edge = b + (side == 1 ? 0 : (long)(n - 1) * st);"),
+    ("table interpolation weight", "f * (P->table[k + 1] - P->table[k])",
+     "f * (P->table[k + 1] + P->table[k])"),
+    ("table interval index", "if (k > P->table_n - 2) k = P->table_n - 2;",
+     "if (k > P->table_n - 3) k = P->table_n - 3;"),
+    ("fixed point sign", "M / (E + table_p(P, E - M * v))", "M / (E + table_p(P, E + M * v))"),
+    ("fixed point stops early", "if (fabs(d) <= OR_FP_TOL) break;", "if (fabs(d) <= 1e-3) break;"),
 ]
 
 
