@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--mode", choices=["full", "kernels"], default="full",
                     help="kernels: only warmup + K steps (for profiler captures)")
-    ap.add_argument("--workload", choices=["single", "batch64", "serve", "tube64", "blast512", "ball200"],
+    ap.add_argument("--workload", choices=["single", "batch64", "serve", "tube64", "blast512", "ball200",
+                                              "table200"],
                     default="single",
                     help="single: one 200^3 hot-spot event (the headline); batch64: 64 events "
                          "of sizes from {48,64,96,128,160}^3 advanced as one batch; serve: a "
@@ -826,6 +827,57 @@ def run_ball(args):
     return 0
 
 
+def run_table(args):
+    """table200: the 200^3 hot-spot state with a tabulated EoS,
+    p = (e/3)(1 - exp(-e/0.3)) at e = k * 0.005 (k < 20001), recovered by the
+    fixed-point iteration of Sec. 3, against the closed-form ideal gas on
+    the same state (FP32 for 60 steps, FP64 for 6)."""
+    import numpy as np
+    import torch
+
+    from paper_1206_0919_gb300 import shasta as S
+    from paper_1206_0919_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    N = 200
+    de = 0.005
+    e_nodes = np.arange(20001) * de
+    table = e_nodes / 3.0 * (1.0 - np.exp(-e_nodes / 0.3))
+    prims = W.hot_spots(N=N, seed=2, n_spots=30)
+    ncell = N ** 3
+    cfg = {"workload": "hot_spots_200^3_tabulated_eos", "grid": [N] * 3,
+           "table": "p = (e/3)(1 - exp(-e/0.3)), 20001 values, de = 0.005, linear",
+           "recovery": "fixed point |v| <- M/(E + p(E - M|v|)), tol 1e-7 (FP32) / 1e-14 (FP64)",
+           "lambda": 0.4, "eta": 0.125, "bc": "reflect", "data": "synthetic"}
+    out = {}
+    for prec, eos, k in (("fp32", "table", 60), ("fp32", "ideal", 60), ("fp64", "table", 6),
+                         ("fp64", "ideal", 6)):
+        kw = dict(table=table, table_de=de) if eos == "table" else {}
+        with S.Solver((N, N, N), precision=prec, eos=eos, stream=stream.cuda_stream, device=local,
+                      **kw) as s:
+            s.set_primitives(*prims.as_list())
+            s.autotune()
+            secs = timed_steps(s, stream, k)
+            out[f"{prec}_{eos}"] = {"value": ncell * k / secs, "unit": UNIT, "steps": k,
+                                    "ms_per_step": secs * 1e3 / k, "clamps": s.counters()}
+    main = out["fp32_table"]
+    if rank == 0:
+        line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": 1,
+                "steps": main["steps"], "warmup": 0, "ms_per_step": main["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic", "config": cfg, "legs": out,
+                "table_vs_closed_form": {p: out[f"{p}_table"]["ms_per_step"] / out[f"{p}_ideal"]["ms_per_step"]
+                                         for p in ("fp32", "fp64")},
+                "cpu_baseline": None,
+                "roofline": {"bound": "hbm", "achieved": ncell * 120 / (main["ms_per_step"] / 1e3) / 1e9,
+                             "peak": measured_peak()[0], "unit": "GB/s"}}
+        line["roofline"]["frac"] = line["roofline"]["achieved"] / line["roofline"]["peak"]
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -840,6 +892,8 @@ def main():
         return run_fixed(args)
     if args.workload == "ball200":
         return run_ball(args)
+    if args.workload == "table200":
+        return run_table(args)
     return run_ours(args)
 
 

@@ -55,8 +55,10 @@ typedef enum shasta_status {
 enum { SHASTA_BC_REFLECT = 0, SHASTA_BC_PERIODIC = 1, SHASTA_BC_FROZEN = 2 };
 
 /* Equation of state.  IDEAL: p = e/3 (Sec. 2).  BAG: p = e/3 for e <= e_c and
- * p = (e - 4B)/3 above (not in the paper; requires 0 <= 4B <= e_c). */
-enum { SHASTA_EOS_IDEAL = 0, SHASTA_EOS_BAG = 1 };
+ * p = (e - 4B)/3 above (not in the paper; requires 0 <= 4B <= e_c).  TABLE:
+ * a tabulated p(e) (Sec. 2 allows tabulated equations of state), recovered
+ * by the fixed-point iteration of Sec. 3; single contexts, FP64 and FP32. */
+enum { SHASTA_EOS_IDEAL = 0, SHASTA_EOS_BAG = 1, SHASTA_EOS_TABLE = 2 };
 
 /* Precision of the device state and arithmetic.  FP64: everything in double.
  * FP32: state, transport, limiter and recovery in float.  MIXED: state,
@@ -75,6 +77,16 @@ typedef struct shasta_eos {
   int kind;   /* SHASTA_EOS_* */
   double B;   /* bag constant (BAG only) */
   double e_c; /* branch point of the bag EoS (BAG only) */
+  /* TABLE only: p at e = k * table_de, k = 0 .. table_n-1 (host memory,
+   * copied by shasta_create), linear in between, the last interval
+   * continued above the table.  Must be finite with p >= 0 and
+   * 0 <= (p[k+1] - p[k]) / table_de < 1 (monotone and causal: the recovery
+   * iteration then contracts).  Recovery: |v| from M/(E + p(E)) by
+   * |v| <- M/(E + p(E - M |v|)) until it changes by at most 1e-14 (FP64) or
+   * 1e-7 (FP32); e = E - M |v|. */
+  const double* table;
+  int table_n;
+  double table_de;
 } shasta_eos;
 
 typedef struct shasta_opts {

@@ -8,6 +8,7 @@
 
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/shasta.h"
 #include "kernels.h"
@@ -38,6 +39,8 @@ struct shasta_ctx {
   float* split_q = nullptr;   // half-step state (quads, R)
   float* split_r = nullptr;
   float* split_scratch = nullptr;
+  void* tab_mem = nullptr;    // tabulated EoS: the table in double, then in float
+  EosTable tab{};
   FieldView view[2] = {};     // where the fields of each buffer live
   float* quad[2] = {};        // FP32 / MIXED: (E, Mx, My, Mz) per cell
   float* rf[2] = {};          // FP32 / MIXED: R
@@ -53,7 +56,7 @@ struct shasta_ctx {
   bool own_stream = false;
   int64_t steps = 0;
   int sm_count = 152;
-  int occ[2][3][2] = {};  // FP32 / MIXED: resident warps per SM [eos][axis][variant]
+  int occ[3][3][2] = {};  // FP32 / MIXED: resident warps per SM [eos][axis][variant]
   int wpb = 4;            // warps per block of the FP32 / MIXED kernels
   long long force_range = 0;  // nonzero: positions per work range (environment override)
   int force_variant = -1; // >= 0: launch variant (environment override)
@@ -103,6 +106,7 @@ EosParams eos_params(const shasta_ctx* c) {
   q.B = c->eos.B;
   q.ec = c->eos.e_c;
   q.omd = 1.0 - c->o.delta;
+  q.tab = c->tab;
   return q;
 }
 
@@ -227,6 +231,7 @@ SweepParams sweep_params(shasta_ctx* c, int axis, int from, int variant, long lo
   P.bag_B = c->eos.B;
   P.bag_ec = c->eos.e_c;
   P.clamp_count = c->d_count;
+  P.tab = c->tab;
   P.range_len = range < 1 ? 1 : range;
   P.variant = variant;
   if (c->o.precision == SHASTA_FP64) {
@@ -357,6 +362,7 @@ void release(shasta_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   cudaFree(c->state_mem);
   cudaFree(c->split_mem);
+  cudaFree(c->tab_mem);
   cudaFree(c->frozen);
   cudaFree(c->staging);
   cudaFree(c->partials);
@@ -426,10 +432,32 @@ shasta_status shasta_create(const shasta_grid* g, double dx, double lambda, cons
     e.B = 0.0;
     e.e_c = 0.0;
   }
-  if (e.kind != SHASTA_EOS_IDEAL && e.kind != SHASTA_EOS_BAG)
+  if (e.kind != SHASTA_EOS_IDEAL && e.kind != SHASTA_EOS_BAG && e.kind != SHASTA_EOS_TABLE)
     return fail(nullptr, SHASTA_EINVAL, "unknown EoS");
   if (e.kind == SHASTA_EOS_BAG && !(e.B >= 0.0 && 4.0 * e.B <= e.e_c))
     return fail(nullptr, SHASTA_EINVAL, "bag EoS needs 0 <= 4B <= e_c");
+  if (e.kind == SHASTA_EOS_TABLE) {
+    if (opts.precision == SHASTA_MIXED)
+      return fail(nullptr, SHASTA_EINVAL, "a tabulated EoS runs in FP64 or FP32");
+    if (opts.scheme == SHASTA_SCHEME_NO_ANTIFLUX && opts.precision == SHASTA_FP32)
+      return fail(nullptr, SHASTA_EINVAL, "no FP32 transport-only kernels for a tabulated EoS");
+    if (!e.table || e.table_n < 2 || e.table_n > (1 << 26) || !(e.table_de > 0.0) ||
+        !isfinite(e.table_de))
+      return fail(nullptr, SHASTA_EINVAL, "table EoS needs a table of >= 2 values and table_de > 0");
+    for (int k = 0; k < e.table_n; ++k) {
+      const double pk = e.table[k];
+      if (!isfinite(pk) || pk < 0.0) return fail(nullptr, SHASTA_EINVAL, "table values must be finite and >= 0");
+      if (k > 0) {
+        const double slope = (pk - e.table[k - 1]) / e.table_de;
+        if (!(slope >= 0.0 && slope < 1.0))
+          return fail(nullptr, SHASTA_EINVAL, "table slopes dp/de must lie in [0, 1)");
+      }
+    }
+  } else {
+    e.table = nullptr;
+    e.table_n = 0;
+    e.table_de = 0.0;
+  }
   int ndev = 0;
   cudaError_t ce = cudaGetDeviceCount(&ndev);
   if (ce != cudaSuccess || ndev < 1)
@@ -485,6 +513,23 @@ shasta_status shasta_create(const shasta_grid* g, double dx, double lambda, cons
         c->view[b].s[k] = 1;
       }
     }
+  }
+  if (e.kind == SHASTA_EOS_TABLE) {
+    const size_t n = (size_t)e.table_n;
+    const size_t b64 = ((n * sizeof(double) + 255) / 256) * 256;
+    err = cudaMalloc(&c->tab_mem, b64 + n * sizeof(float));
+    if (err != cudaSuccess) return bail(err, "cudaMalloc EoS table");
+    std::vector<float> t32(e.table, e.table + n);
+    err = cudaMemcpy(c->tab_mem, e.table, n * sizeof(double), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess)
+      err = cudaMemcpy((char*)c->tab_mem + b64, t32.data(), n * sizeof(float), cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) return bail(err, "copy EoS table");
+    c->tab.p64 = (const double*)c->tab_mem;
+    c->tab.p32 = (const float*)((char*)c->tab_mem + b64);
+    c->tab.n = e.table_n;
+    c->tab.de = e.table_de;
+    c->tab.inv_de32 = (float)(1.0 / e.table_de);
+    c->eos.table = nullptr;  // the caller's memory is not kept
   }
   if (opts.scheme == SHASTA_SCHEME_SPLIT) {
     const size_t half = ((c->ncell * 20 + 255) / 256) * 256;

@@ -39,6 +39,7 @@ __device__ __forceinline__ T& fv(const FieldView& v, int k, size_t i) {
 }
 
 __device__ __forceinline__ double eos_p(const EosParams& q, double e) {
+  if (q.kind == EOS_TABLE) return table_p64(q.tab, e);
   if (q.kind == EOS_BAG && e > q.ec) return (e - 4.0 * q.B) / 3.0;
   return e / 3.0;
 }
@@ -89,7 +90,9 @@ __global__ void k_recover(Rec6 r, size_t n, EosParams q) {
         scale = lim / M;
         M = lim;
       }
-      if (q.kind == EOS_BAG)
+      if (q.kind == EOS_TABLE)
+        eos_table_solve(E, M, q.tab, e, pp);
+      else if (q.kind == EOS_BAG)
         eos_solve<double, EOS_BAG>(E, M, q.B, q.ec, e, pp);
       else
         eos_solve<double, EOS_IDEAL>(E, M, q.B, q.ec, e, pp);

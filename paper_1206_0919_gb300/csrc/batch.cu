@@ -79,7 +79,7 @@ struct shasta_batch {
   double* d_tot = nullptr;
   double* h_small = nullptr;  // pinned
   int sm_count = 152;
-  int occ[2][3][2] = {};
+  int occ[3][3][2] = {};
   int wpb = 4;
   // launch choice per axis: register variant and positions per work range
   bool tuned = false;

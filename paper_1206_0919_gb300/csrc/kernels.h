@@ -17,12 +17,12 @@ cudaError_t launch_sweep_mixed(const SweepParams& P, int axis, int eos, cudaStre
 // Sets the shared-memory attribute of every FP32 / mixed sweep kernel and
 // reports resident warps per SM as [eos][axis][variant].  Call once per
 // device before the first launch (and before any stream capture).
-cudaError_t prepare_sweep_f32(int occupancy[2][3][2]);
-cudaError_t prepare_sweep_mixed(int occupancy[2][3][2]);
+cudaError_t prepare_sweep_f32(int occupancy[3][3][2]);
+cudaError_t prepare_sweep_mixed(int occupancy[3][3][2]);
 int sweep_warps_per_block_f32();
 // FP32 sweeps without the antidiffusion stage (sweep_f32_noaf.cu), same
 // launch parameters and occupancy layout as the fused FP32 sweeps.
-cudaError_t prepare_sweep_f32_noaf(int occupancy[2][3][2]);
+cudaError_t prepare_sweep_f32_noaf(int occupancy[3][3][2]);
 cudaError_t launch_sweep_f32_noaf(const SweepParams& P, int axis, int eos, cudaStream_t s);
 // The split scheme (sweep_split.cu): one FP32 sweep as recovery, transport
 // and antidiffusion kernels with intermediates in device memory.  half_q /
@@ -34,8 +34,8 @@ cudaError_t launch_sweep_split(const SweepParams& P, int axis, int eos, float* s
 int sweep_warps_per_block_mixed();
 // Batched FP32 / MIXED sweeps (one launch over the work list L, all along
 // `axis`); prepare_* as above for the batched kernels.
-cudaError_t prepare_batch_f32(int occupancy[2][3][2]);
-cudaError_t prepare_batch_mixed(int occupancy[2][3][2]);
+cudaError_t prepare_batch_f32(int occupancy[3][3][2]);
+cudaError_t prepare_batch_mixed(int occupancy[3][3][2]);
 cudaError_t launch_batch_f32(const SweepParams& P, const BatchList& L, int axis, int eos,
                              cudaStream_t s);
 cudaError_t launch_batch_mixed(const SweepParams& P, const BatchList& L, int axis, int eos,
@@ -54,7 +54,8 @@ struct FieldView {
 struct EosParams {
   int kind;
   double B, ec;
-  double omd;  // 1 - delta
+  double omd;    // 1 - delta
+  EosTable tab;  // EOS_TABLE
 };
 
 // Auxiliary kernels (aux.cu).  `is32` selects float (1) or double (0) storage.

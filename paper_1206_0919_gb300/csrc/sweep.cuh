@@ -40,7 +40,18 @@ constexpr int NF = 5;  // E, M_x, M_y, M_z, R
 constexpr int NG = 3;  // ghost depth of one SHASTA pass
 
 enum { BC_REFLECT = 0, BC_PERIODIC = 1, BC_FROZEN = 2 };
-enum { EOS_IDEAL = 0, EOS_BAG = 1 };
+enum { EOS_IDEAL = 0, EOS_BAG = 1, EOS_TABLE = 2 };
+
+// Tabulated EoS (EOS_TABLE): p at e = k de, k = 0 .. n-1, linear in
+// between, the last interval continued above the table (device copies in
+// double and float).
+struct EosTable {
+  const double* p64;
+  const float* p32;
+  int n;
+  double de;
+  float inv_de32;  // 1 / de in float (FP32 lookups)
+};
 
 // Geometry and constants of one sweep launch (filled on the host).
 struct SweepParams {
@@ -68,6 +79,7 @@ struct SweepParams {
   const float* rin;
   float* qout;
   float* rout;
+  EosTable tab;  // EOS_TABLE only
 };
 
 // Batched sweeps: one event of a batch.  All events of a batch share the
@@ -131,13 +143,41 @@ __device__ __forceinline__ void eos_solve(R E, R M, R B, R ec, R& e, R& p) {
   }
 }
 
+// p(e) of the table, the lookup written as in the oracle.
+__device__ __forceinline__ double table_p64(const EosTable& T, double e) {
+  double x = e / T.de;
+  int k = (int)floor(x);
+  if (k < 0) k = 0;
+  if (k > T.n - 2) k = T.n - 2;
+  double f = x - (double)k;
+  const double a = T.p64[k], b = T.p64[k + 1];
+  return a + f * (b - a);
+}
+
+// Tabulated EoS: |v| by the fixed-point iteration of Sec. 3 (kept by the
+// paper so that a table can replace p = e/3): from v = M/(E + p(E)),
+// v <- M/(E + p(E - M v)) until the change is at most 1e-14 (200 at most),
+// then e = E - M v and p = p(e).
+__device__ __forceinline__ void eos_table_solve(double E, double M, const EosTable& T, double& e,
+                                                double& p) {
+  double v = M / (E + table_p64(T, E));
+  for (int it = 0; it < 200; ++it) {
+    const double vn = M / (E + table_p64(T, E - M * v));
+    const double d = vn - v;
+    v = vn;
+    if (fabs(d) <= 1e-14) break;
+  }
+  e = E - M * v;
+  p = table_p64(T, e);
+}
+
 // Velocity along the sweep axis and pressure of one cell.  m1 is the
 // momentum along the sweep, m2/m3 the other two in increasing axis order;
 // |M|^2 is summed in x, y, z order.
 // Returns 1 if |M| was clamped or E <= 0, else 0.
 template <class R, int EOS, int AXIS>
-__device__ __forceinline__ unsigned recover_wp(R E, R m1, R m2, R m3, R omd, R B, R ec, R& w,
-                                               R& p) {
+__device__ __forceinline__ unsigned recover_wp(R E, R m1, R m2, R m3, R omd, R B, R ec,
+                                               const EosTable& T, R& w, R& p) {
   if (!(E > R(0))) {
     w = R(0);
     p = R(0);
@@ -156,7 +196,10 @@ __device__ __forceinline__ unsigned recover_wp(R E, R m1, R m2, R m3, R omd, R B
     clamped = 1;
   }
   R e, pp;
-  eos_solve<R, EOS>(E, M, B, ec, e, pp);
+  if constexpr (EOS == EOS_TABLE)
+    eos_table_solve(E, M, T, e, pp);
+  else
+    eos_solve<R, EOS>(E, M, B, ec, e, pp);
   R h = E + pp;
   w = m / h;
   p = pp;
@@ -343,7 +386,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(SweepParams P) {
     {
       R w, p;
       const unsigned c0 = recover_wp<R, EOS, AXIS>(R(u[7][0]), R(u[7][1]), R(u[7][2]),
-                                                   R(u[7][3]), omd, B, ec, w, p);
+                                                   R(u[7][3]), omd, B, ec, P.tab, w, p);
       nclamp += (q >= s0 && q < s1) ? c0 : 0u;
       wn[2] = T(w);
       pn[2] = T(p);
@@ -384,7 +427,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(SweepParams P) {
     {
       R w, p;
       // (the counter counts level-n recoveries only, as the FP32 kernels)
-      recover_wp<R, EOS, AXIS>(R(hs[0]), R(hs[1]), R(hs[2]), R(hs[3]), omd, B, ec, w, p);
+      recover_wp<R, EOS, AXIS>(R(hs[0]), R(hs[1]), R(hs[2]), R(hs[3]), omd, B, ec, P.tab, w, p);
       wh[2] = T(w);
       ph[2] = T(p);
     }

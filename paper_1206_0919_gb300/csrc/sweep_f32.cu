@@ -3,7 +3,7 @@
 
 namespace shasta {
 
-cudaError_t prepare_sweep_f32(int occupancy[2][3][2]) {
+cudaError_t prepare_sweep_f32(int occupancy[3][3][2]) {
   return launch::prepare<false, launch::SINGLE>(occupancy);
 }
 

@@ -24,6 +24,9 @@ cudaError_t launch_sweep_f64(const SweepParams& P, int axis, int eos, cudaStream
     case 3: return go<EOS_BAG, 0>(P, s);
     case 4: return go<EOS_BAG, 1>(P, s);
     case 5: return go<EOS_BAG, 2>(P, s);
+    case 6: return go<EOS_TABLE, 0>(P, s);
+    case 7: return go<EOS_TABLE, 1>(P, s);
+    case 8: return go<EOS_TABLE, 2>(P, s);
   }
   return cudaErrorInvalidValue;
 }

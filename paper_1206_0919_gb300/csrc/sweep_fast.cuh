@@ -273,12 +273,41 @@ __device__ __forceinline__ void copy_cell(const SweepParams& P, const Geo& G, fl
 
 // ----------------------------------------------------------- recovery ----
 
+// p(e) of a tabulated EoS in float: linear between the nodes k de, the
+// last interval continued above (the index stays inside the table for any
+// e, NaN included).
+__device__ __forceinline__ float tab32(const EosTable& T, float e) {
+  const float x = e * T.inv_de32;
+  int k = (int)x;
+  k = k < 0 ? 0 : (k > T.n - 2 ? T.n - 2 : k);
+  const float f = x - (float)k;
+  const float a = __ldg(T.p32 + k), b = __ldg(T.p32 + k + 1);
+  return fmaf(f, b - a, a);
+}
+
+// Tabulated EoS: p from E and |M|^2 by the fixed-point iteration of Sec. 3,
+// |v| <- |M| / (E + p(E - |M| |v|)) from |v| = |M| / (E + p(E)), until the
+// change is at most 1e-7 (40 iterations at most).
+__device__ __forceinline__ float table_p32(const EosTable& T, float E, float M2) {
+  const float M = sqrtf(M2);
+  float v = M * __fdividef(1.0f, E + tab32(T, E));
+#pragma unroll 1
+  for (int it = 0; it < 40; ++it) {
+    const float vn = M * __fdividef(1.0f, E + tab32(T, fmaf(-M, v, E)));
+    const float d = vn - v;
+    v = vn;
+    if (fabsf(d) <= 1e-7f) break;
+  }
+  return tab32(T, fmaf(-M, v, E));
+}
+
 // Velocity along the sweep and pressure of one cell, FP32 (MIXED: D in
 // double-float).  mx, my, mz are the momenta, m1 the one along the sweep.
 // Returns 1 if |M| was clamped or E <= 0.
 template <int EOS, bool MIXED>
 __device__ __forceinline__ unsigned rec32(float E, float mx, float my, float mz, float m1,
-                                          float omd, float B, float ec, float& w, float& p) {
+                                          float omd, float B, float ec, const EosTable& T,
+                                          float& w, float& p) {
   unsigned clamped = 0;
   float M2 = fmaf(mx, mx, fmaf(my, my, mz * mz));
   const float E2 = E * E;
@@ -311,21 +340,26 @@ __device__ __forceinline__ unsigned rec32(float E, float mx, float my, float mz,
   } else {
     D = E2 - M2;
   }
-  D = fmaxf(D, 0.0f);
-  const float s = sqrtf(fmaf(3.0f, D, E2));
-  float pp = D * __fdividef(1.0f, E + s);
-  if (EOS == EOS_BAG) {
-    if (3.0f * pp > ec) {
-      const float r = 4.0f * (E - B) * (E - B) - 3.0f * M2;
-      bool ok = false;
-      if (E > ec && r >= 0.0f) {
-        const float eb = __fdividef(3.0f * D - 4.0f * B * E, sqrtf(r) + (E - 2.0f * B));
-        if (eb > ec) {
-          pp = (eb - 4.0f * B) * (1.0f / 3.0f);
-          ok = true;
+  float pp;
+  if constexpr (EOS == EOS_TABLE) {
+    pp = table_p32(T, E, M2);
+  } else {
+    D = fmaxf(D, 0.0f);
+    const float s = sqrtf(fmaf(3.0f, D, E2));
+    pp = D * __fdividef(1.0f, E + s);
+    if (EOS == EOS_BAG) {
+      if (3.0f * pp > ec) {
+        const float r = 4.0f * (E - B) * (E - B) - 3.0f * M2;
+        bool ok = false;
+        if (E > ec && r >= 0.0f) {
+          const float eb = __fdividef(3.0f * D - 4.0f * B * E, sqrtf(r) + (E - 2.0f * B));
+          if (eb > ec) {
+            pp = (eb - 4.0f * B) * (1.0f / 3.0f);
+            ok = true;
+          }
         }
+        if (!ok) pp = __fdividef(M2, E - ec) - E;
       }
-      if (!ok) pp = __fdividef(M2, E - ec) - E;
     }
   }
   w = m * __fdividef(1.0f, E + pp);
@@ -344,11 +378,12 @@ __device__ __forceinline__ unsigned rec32(float E, float mx, float my, float mz,
 // the piece's own positions) and it was clamped or vacuum.
 template <int EOS, bool MIXED>
 __device__ __forceinline__ void rec2(f2 E, f2 mx, f2 my, f2 mz, f2 mpar, float omd, float B,
-                                     float ec, f2& w, f2& p, unsigned& cnt, bool in_seg) {
+                                     float ec, const EosTable& T, f2& w, f2& p, unsigned& cnt,
+                                     bool in_seg) {
   float wl, wh, pl, ph;
-  const unsigned c = rec32<EOS, MIXED>(E.x, mx.x, my.x, mz.x, mpar.x, omd, B, ec, wl, pl);
+  const unsigned c = rec32<EOS, MIXED>(E.x, mx.x, my.x, mz.x, mpar.x, omd, B, ec, T, wl, pl);
   if (c) cnt += in_seg ? 1u : 0u;
-  rec32<EOS, MIXED>(E.y, mx.y, my.y, mz.y, mpar.y, omd, B, ec, wh, ph);
+  rec32<EOS, MIXED>(E.y, mx.y, my.y, mz.y, mpar.y, omd, B, ec, T, wh, ph);
   w = f2{wl, wh};
   p = f2{pl, ph};
 }
@@ -662,7 +697,7 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, i
       f2 w2, p2;
       // count each cell of the piece once (lanes past the last line only
       // repeat it)
-      rec2<EOS, MIXED>(E, mx, my, mz, mpar, omd, B, ec, w2, p2, nclamp,
+      rec2<EOS, MIXED>(E, mx, my, mz, mpar, omd, B, ec, P.tab, w2, p2, nclamp,
                        valid && (unsigned)(q - s0) < (unsigned)(s1 - s0));
       float pl, phi, pwl, pwh;
       up(w2, wn0, wh0);

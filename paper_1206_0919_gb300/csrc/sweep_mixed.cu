@@ -4,7 +4,7 @@
 
 namespace shasta {
 
-cudaError_t prepare_sweep_mixed(int occupancy[2][3][2]) {
+cudaError_t prepare_sweep_mixed(int occupancy[3][3][2]) {
   return launch::prepare<true, launch::SINGLE>(occupancy);
 }
 

@@ -94,7 +94,7 @@ __global__ void k_recover(SweepParams P, St s, int axis, Ext X, float* w, float*
     load(P, s, t, j, axis, u);
     float wv, pv;
     c = fast::rec32<EOS, false>(u[0], u[1], u[2], u[3], u[1 + axis], float(P.omd), float(P.bag_B),
-                                float(P.bag_ec), wv, pv);
+                                float(P.bag_ec), P.tab, wv, pv);
     w[X.at(j, t)] = wv;
     p[X.at(j, t)] = pv;
     c = count && j >= 0 && j < P.n ? c : 0u;
@@ -211,6 +211,8 @@ cudaError_t launch_sweep_split(const SweepParams& P, int axis, int eos, float* s
     const St src = pass == 0 ? old : half;
     if (eos == EOS_BAG)
       k_recover<EOS_BAG><<<blocks_for(nw), kThreads, 0, s>>>(P, src, axis, W, w, p, pass == 0);
+    else if (eos == EOS_TABLE)
+      k_recover<EOS_TABLE><<<blocks_for(nw), kThreads, 0, s>>>(P, src, axis, W, w, p, pass == 0);
     else
       k_recover<EOS_IDEAL><<<blocks_for(nw), kThreads, 0, s>>>(P, src, axis, W, w, p, pass == 0);
     const float tau = float(pass == 0 ? P.tau_h : P.tau_f);

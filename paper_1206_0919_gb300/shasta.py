@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "libshasta.so")
 
 OK, EINVAL, ENOMEM, EAGAIN, EUNPHYSICAL, ETIMEOUT, ECUDA, ENOTFOUND = range(8)
 BC_REFLECT, BC_PERIODIC, BC_FROZEN = 0, 1, 2
-EOS_IDEAL, EOS_BAG = 0, 1
+EOS_IDEAL, EOS_BAG, EOS_TABLE = 0, 1, 2
 FP64, FP32, MIXED = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 
@@ -40,7 +40,8 @@ class Grid(C.Structure):
 
 
 class Eos(C.Structure):
-    _fields_ = [("kind", C.c_int), ("B", C.c_double), ("e_c", C.c_double)]
+    _fields_ = [("kind", C.c_int), ("B", C.c_double), ("e_c", C.c_double),
+                ("table", C.POINTER(C.c_double)), ("table_n", C.c_int), ("table_de", C.c_double)]
 
 
 class Opts(C.Structure):
@@ -246,13 +247,20 @@ class Solver:
 
     def __init__(self, shape, lam=0.4, dx=1.0, precision="fp32", bc="reflect", eos="ideal",
                  bag_B=0.1, bag_ec=0.5, eta=0.125, delta=0.0, stream=None, device=0,
-                 check_input=True, autotune=True, use_graphs=True, scheme="fused"):
+                 check_input=True, autotune=True, use_graphs=True, scheme="fused", table=None,
+                 table_de=0.0):
         L = lib()
         nx, ny, nz = shape
         self.shape = (nx, ny, nz)
         g = Grid(nx, ny, nz, BCS[bc] if isinstance(bc, str) else bc)
-        kind = {"ideal": EOS_IDEAL, "bag": EOS_BAG}[eos] if isinstance(eos, str) else eos
+        kind = {"ideal": EOS_IDEAL, "bag": EOS_BAG, "table": EOS_TABLE}[eos] \
+            if isinstance(eos, str) else eos
         e = Eos(kind, bag_B, bag_ec)
+        if table is not None:
+            t = np.ascontiguousarray(table, dtype=np.float64)  # copied by shasta_create
+            e.table = t.ctypes.data_as(C.POINTER(C.c_double))
+            e.table_n = t.size
+            e.table_de = table_de
         o = Opts()
         L.shasta_default_opts(C.byref(o))
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else precision

@@ -68,6 +68,24 @@ def test_bad_scheme_is_rejected_before_any_device_call(lib):
         assert ei.value.status == S.EINVAL, kw
 
 
+def test_bad_eos_tables_are_rejected(lib):
+    """A tabulated EoS must be finite, p >= 0, monotone and causal
+    (0 <= dp/de < 1), with at least two values and table_de > 0; MIXED has
+    no tabulated path.  All are option errors found before any device call."""
+    import numpy as np
+    good = np.arange(10) * 0.1 / 3.0
+    bad = [dict(table=good[:1], table_de=0.1), dict(table=good, table_de=0.0),
+           dict(table=-good - 1.0, table_de=0.1), dict(table=good[::-1].copy(), table_de=0.1),
+           dict(table=np.arange(10) * 0.1 * 1.5, table_de=0.1),
+           dict(table=np.where(np.arange(10) == 4, np.nan, good), table_de=0.1),
+           dict(table=good, table_de=0.1, precision="mixed"),
+           dict(table=good, table_de=0.1, scheme="no_antiflux")]
+    for kw in bad:
+        with pytest.raises(S.ShastaError) as ei:
+            S.Solver((4, 4, 4), eos="table", **kw)
+        assert ei.value.status == S.EINVAL, kw
+
+
 def test_batch_and_server_without_gpu_fail_cleanly(lib):
     try:
         import torch
