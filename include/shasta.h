@@ -81,9 +81,10 @@ typedef struct shasta_eos {
    * copied by shasta_create), linear in between, the last interval
    * continued above the table.  Must be finite with p >= 0 and
    * 0 <= (p[k+1] - p[k]) / table_de < 1 (monotone and causal: the recovery
-   * iteration then contracts).  Recovery: |v| from M/(E + p(E)) by
-   * |v| <- M/(E + p(E - M |v|)) until it changes by at most 1e-14 (FP64) or
-   * 1e-7 (FP32); e = E - M |v|. */
+   * iteration then contracts).  Recovery: the root of
+   * |v| = M/(E + p(E - M |v|)) from |v| = M/(E + p(E)): FP64 iterates that
+   * map until |v| changes by at most 1e-14, FP32 takes Newton steps on it
+   * to a change of 1e-7; e = E - M |v|. */
   const double* table;
   int table_n;
   double table_de;

@@ -275,27 +275,36 @@ __device__ __forceinline__ void copy_cell(const SweepParams& P, const Geo& G, fl
 
 // p(e) of a tabulated EoS in float: linear between the nodes k de, the
 // last interval continued above (the index stays inside the table for any
-// e, NaN included).
-__device__ __forceinline__ float tab32(const EosTable& T, float e) {
+// e, NaN included); *slope receives dp/de of the interval.
+__device__ __forceinline__ float tab32(const EosTable& T, float e, float* slope = nullptr) {
   const float x = e * T.inv_de32;
   int k = (int)x;
   k = k < 0 ? 0 : (k > T.n - 2 ? T.n - 2 : k);
   const float f = x - (float)k;
   const float a = __ldg(T.p32 + k), b = __ldg(T.p32 + k + 1);
+  if (slope) *slope = (b - a) * T.inv_de32;
   return fmaf(f, b - a, a);
 }
 
-// Tabulated EoS: p from E and |M|^2 by the fixed-point iteration of Sec. 3,
-// |v| <- |M| / (E + p(E - |M| |v|)) from |v| = |M| / (E + p(E)), until the
-// change is at most 1e-7 (40 iterations at most).
+// Tabulated EoS: p from E and |M|^2.  The root is the fixed point of Sec. 3,
+// |v| = |M| / (E + p(E - |M| |v|)), started as there from |M| / (E + p(E)).
+// In float the root is found by Newton steps on g(v) = v - |M| / (E + p),
+// g'(v) = 1 - |M|^2 p'(e) / (E + p)^2 >= 1 - v^2 p' > 0 (exact within one
+// interval of the piecewise-linear table), until the change is at most
+// 1e-7 (12 steps at most), then p = p(E - |M| |v|).
 __device__ __forceinline__ float table_p32(const EosTable& T, float E, float M2) {
   const float M = sqrtf(M2);
   float v = M * __fdividef(1.0f, E + tab32(T, E));
 #pragma unroll 1
-  for (int it = 0; it < 40; ++it) {
-    const float vn = M * __fdividef(1.0f, E + tab32(T, fmaf(-M, v, E)));
-    const float d = vn - v;
-    v = vn;
+  for (int it = 0; it < 12; ++it) {
+    float dp;
+    const float pe = tab32(T, fmaf(-M, v, E), &dp);
+    const float r = __fdividef(1.0f, E + pe);
+    const float g = fmaf(-M, r, v);               // v - M / (E + p)
+    const float mr = M * r;
+    const float gp = fmaf(-mr * mr, dp, 1.0f);    // 1 - M^2 p' / (E + p)^2
+    const float d = __fdividef(g, gp);
+    v -= d;
     if (fabsf(d) <= 1e-7f) break;
   }
   return tab32(T, fmaf(-M, v, E));
