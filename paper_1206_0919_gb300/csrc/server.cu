@@ -86,6 +86,28 @@ struct Piece {
 
 // Device -> host (pageable) for a list of pieces of at most kBounceHalf
 // bytes, through `st`; returns when every piece is in place.
+// Copies len bytes with kCopyThreads threads (the callers' arrays are often
+// fresh: first-touch page faults dominate a single-threaded copy); falls
+// back to one thread if no thread can be started.
+constexpr int kCopyThreads = 4;
+void par_copy(char* dst, const char* src, size_t len) {
+  const size_t part = ((len + kCopyThreads - 1) / kCopyThreads + 4095) & ~(size_t)4095;
+  std::thread th[kCopyThreads - 1];
+  for (int t = 1; t < kCopyThreads; ++t) {
+    const size_t o = (size_t)t * part;
+    if (o >= len) break;
+    const size_t n = std::min(part, len - o);
+    try {
+      th[t - 1] = std::thread([=] { memcpy(dst + o, src + o, n); });
+    } catch (...) {
+      memcpy(dst + o, src + o, n);
+    }
+  }
+  memcpy(dst, src, std::min(part, len));
+  for (auto& x : th)
+    if (x.joinable()) x.join();
+}
+
 cudaError_t bounce_d2h(Bounce& b, const std::vector<Piece>& pcs, cudaStream_t st) {
   auto issue = [&](size_t k) {
     const int h = (int)(k & 1);
@@ -97,7 +119,7 @@ cudaError_t bounce_d2h(Bounce& b, const std::vector<Piece>& pcs, cudaStream_t st
   for (size_t k = 0; k < pcs.size() && e == cudaSuccess; ++k) {
     if (k + 1 < pcs.size()) e = issue(k + 1);  // its half was emptied in step k - 1
     if (e == cudaSuccess) e = cudaEventSynchronize(b.done[k & 1]);
-    if (e == cudaSuccess) memcpy(pcs[k].dst, b.buf + (k & 1) * kBounceHalf, pcs[k].len);
+    if (e == cudaSuccess) par_copy(pcs[k].dst, b.buf + (k & 1) * kBounceHalf, pcs[k].len);
   }
   return e;
 }

@@ -352,24 +352,26 @@ __device__ __forceinline__ unsigned rec32(float E, float mx, float my, float mz,
   float pp;
   if constexpr (EOS == EOS_TABLE) {
     pp = table_p32(T, E, M2);
+  } else if constexpr (EOS == EOS_BAG) {
+    // One root for both branches.  The ideal-gas root e lies above e_c
+    // exactly when (E - e_c)(E + e_c/3) > |M|^2, i.e. 3D > e_c (2E + e_c);
+    // then the bag root with p = (e - 4b)/3, else b = 0, which is the
+    // ideal-gas root itself (p = D / (E + sqrt(E^2 + 3D))):
+    //   e + ... : p = (D - 4bE/3) / (E - 2b + sqrt(3D + (E - 4b)^2 - 12b^2)) - 4b/3.
+    D = fmaxf(D, 0.0f);
+    const bool bag = 3.0f * D > ec * fmaf(2.0f, E, ec);
+    const float b = bag ? B : 0.0f;
+    const float q = fmaf(-4.0f, b, E);
+    const float r = fmaf(3.0f, D, fmaf(q, q, -12.0f * (b * b)));
+    const float s = sqrtf(fmaxf(r, 0.0f));
+    pp = fmaf(-(4.0f / 3.0f) * b, E, D) * __fdividef(1.0f, fmaf(-2.0f, b, E + s)) - (4.0f / 3.0f) * b;
+    // the bag root must exist and lie above e_c; else the mixed-phase point
+    if (bag && !(E > ec && r >= 0.0f && fmaf(3.0f, pp, 4.0f * B) > ec))
+      pp = __fdividef(M2, E - ec) - E;
   } else {
     D = fmaxf(D, 0.0f);
     const float s = sqrtf(fmaf(3.0f, D, E2));
     pp = D * __fdividef(1.0f, E + s);
-    if (EOS == EOS_BAG) {
-      if (3.0f * pp > ec) {
-        const float r = 4.0f * (E - B) * (E - B) - 3.0f * M2;
-        bool ok = false;
-        if (E > ec && r >= 0.0f) {
-          const float eb = __fdividef(3.0f * D - 4.0f * B * E, sqrtf(r) + (E - 2.0f * B));
-          if (eb > ec) {
-            pp = (eb - 4.0f * B) * (1.0f / 3.0f);
-            ok = true;
-          }
-        }
-        if (!ok) pp = __fdividef(M2, E - ec) - E;
-      }
-    }
   }
   w = m * __fdividef(1.0f, E + pp);
   p = pp;
