@@ -324,8 +324,10 @@ bool harvest(shasta_server* s) {
   return true;
 }
 
-// Admits staged jobs into the batch, in order, while the pool has room.
+// Admits staged jobs into the batch, in order, while the pool has room;
+// only at phase 0 of the resident events (so that they stay in step).
 bool admit(shasta_server* s) {
+  if (!s->resident.empty() && s->resident.front()->steps % 6 != 0) return true;
   size_t i = 0;
   for (; i < s->staged.size(); ++i) {
     const JobP& j = s->staged[i];
@@ -397,7 +399,11 @@ void worker_main(shasta_server* s) {
     if (!harvest(s)) break;
     lap(2);
     if (!s->resident.empty()) {
-      int64_t k = s->o.steps_per_round;
+      // every resident event is at the same phase of the six-step axis
+      // table (events join only at phase 0), so each sweep slot sweeps one
+      // axis: one launch per EoS.  Rounds end on six-step boundaries.
+      const int64_t phase = s->resident.front()->steps % 6;
+      int64_t k = std::min<int64_t>(s->o.steps_per_round, 6 - phase);
       for (const JobP& j : s->resident) k = std::min(k, j->steps_left);
       if (shasta_batch_step(s->batch, (int)k) != SHASTA_OK) {
         stop_all(s, batch_msg(s, "step"));
