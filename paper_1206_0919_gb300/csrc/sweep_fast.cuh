@@ -331,21 +331,20 @@ __device__ __forceinline__ unsigned rec32(float E, float mx, float my, float mz,
     D = E2 - M2;
     clamped = 1;
   } else if (MIXED) {
-    // D = E^2 - mx^2 - my^2 - mz^2 from exact products and compensated sums
-    const float e_l = fmaf(E, E, -E2);
+    // D = E^2 - |M|^2 with |M|^2 = hi + lo from error-free products and
+    // compensated sums; E^2 - hi in one fused multiply-add (one rounding of
+    // the exact difference), then lo
     const float a = mx * mx, a_l = fmaf(mx, mx, -a);
     const float b = my * my, b_l = fmaf(my, my, -b);
     const float c = mz * mz, c_l = fmaf(mz, mz, -c);
-    const float s1 = E2 - a;
-    float bb = s1 - E2;
-    const float r1 = (E2 - (s1 - bb)) + (-a - bb);
-    const float s2 = s1 - b;
-    bb = s2 - s1;
-    const float r2 = (s1 - (s2 - bb)) + (-b - bb);
-    const float s3 = s2 - c;
-    bb = s3 - s2;
-    const float r3 = (s2 - (s3 - bb)) + (-c - bb);
-    D = s3 + (((r1 + r2) + r3) + (((e_l - a_l) - b_l) - c_l));
+    const float s1 = a + b;
+    float bb = s1 - a;
+    const float r1 = (a - (s1 - bb)) + (b - bb);
+    const float hi = s1 + c;
+    bb = hi - s1;
+    const float r2 = (s1 - (hi - bb)) + (c - bb);
+    const float lo = ((a_l + b_l) + c_l) + (r1 + r2);
+    D = fmaf(E, E, -hi) - lo;
   } else {
     D = E2 - M2;
   }
