@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--rate", type=float, default=200.0, help="serve: arrivals per second per rank")
     ap.add_argument("--max-resident", type=int, default=64, help="serve: events resident at once")
     ap.add_argument("--budget-gb", type=float, default=48.0, help="serve: device memory budget")
-    ap.add_argument("--steps-per-round", type=int, default=4,
+    ap.add_argument("--steps-per-round", type=int, default=6,
                     help="serve: steps enqueued between admission checks")
     return ap.parse_args()
 

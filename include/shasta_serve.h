@@ -41,7 +41,10 @@ typedef struct shasta_server_opts {
   int64_t staging_bytes;    /* the staging part of the budget (half input, half output); 0: an eighth */
   int max_resident;         /* events advanced together at most (default 256) */
   int max_queue;            /* submitted events not yet resident at most (default 4096) */
-  int steps_per_round;      /* steps enqueued between admission checks (default 4) */
+  int steps_per_round;      /* at most this many steps between admission checks
+                               (default 6).  Events join only at phase 0 of the
+                               resident events' six-step axis cycle, and rounds
+                               end on those boundaries */
 } shasta_server_opts;
 
 /* One event.  fields: five host arrays (E, Mx, My, Mz, R) or (e, vx, vy,

@@ -506,7 +506,7 @@ void shasta_server_default_opts(shasta_server_opts* o) {
   o->staging_bytes = 0;
   o->max_resident = 256;
   o->max_queue = 4096;
-  o->steps_per_round = 4;
+  o->steps_per_round = 6;
 }
 
 shasta_status shasta_server_create(const shasta_server_opts* o, shasta_server** out) {

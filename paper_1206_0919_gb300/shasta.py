@@ -501,7 +501,7 @@ class Server:
     poll for their results."""
 
     def __init__(self, hbm_budget_bytes, precision="fp32", staging_bytes=0, max_resident=256,
-                 max_queue=4096, steps_per_round=4, eta=0.125, delta=0.0, device=0):
+                 max_queue=4096, steps_per_round=6, eta=0.125, delta=0.0, device=0):
         L = lib()
         o = ServerOpts()
         L.shasta_server_default_opts(C.byref(o))

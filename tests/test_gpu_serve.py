@@ -65,6 +65,9 @@ def test_results_same_alone_and_in_the_mix(precision):
         st = srv.stats()
     assert st["finished"] == len(MIX) and st["failed"] == 0
     assert st["peak_resident"] >= 2, st  # events really shared the batch
+    # resident events stay at one phase of the axis table: every sweep slot
+    # sweeps one axis, at most one launch per EoS (2 EoS x 3 slots a step)
+    assert st["sweep_launches"] <= 6 * st["batch_steps"], st
     for (sh, eos, k, seed), a, m in zip(MIX, alone, mixed):
         assert a["steps"] == m["steps"] == k
         for key in ("e", "vx", "vy", "vz", "n", "p"):
