@@ -401,10 +401,12 @@ __device__ __forceinline__ void rec2(f2 E, f2 mx, f2 my, f2 mz, f2 mpar, float o
 // ------------------------------------------------------- antidiffusion ----
 
 // Flux limiter of Sec. 3 on one field: A = s max(0, min(s dhp, |aph|, s dhm))
-// with s = sgn(aph) (aph = 0 gives 0), written without the sign: for
-// aph > 0 only the first term can be nonzero, for aph < 0 only the second.
+// with s = sgn(aph) (aph = 0 gives 0), written without the sign as
+// max(lo, min(hi, 0)) with lo = min3(dhp, aph, dhm), hi = max3(...): for
+// aph > 0, hi >= aph > 0 and the result is max(lo, 0); for aph < 0,
+// lo <= aph <= min(hi, 0) and the result is min(hi, 0); for aph = 0 it is 0.
 __device__ __forceinline__ float limit(float aph, float dhp, float dhm) {
-  return fmaxf(min3f(dhp, aph, dhm), 0.0f) + fminf(max3f(dhp, aph, dhm), 0.0f);
+  return fmaxf(min3f(dhp, aph, dhm), fminf(max3f(dhp, aph, dhm), 0.0f));
 }
 
 // ------------------------------------------------------ line pipeline ----

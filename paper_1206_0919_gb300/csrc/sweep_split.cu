@@ -135,7 +135,7 @@ __global__ void k_transport(SweepParams P, St s, int axis, Ext X, Ext W, const f
 }
 
 __device__ __forceinline__ float limit(float aph, float dhp, float dhm) {
-  return fmaxf(fast::min3f(dhp, aph, dhm), 0.0f) + fminf(fast::max3f(dhp, aph, dhm), 0.0f);
+  return fast::limit(aph, dhp, dhm);
 }
 
 // U'_j = Uhat_j - A_j + A_{j-1} on [0, n): A from Uhat (buffer U of
