@@ -338,7 +338,7 @@ bool admit(shasta_server* s) {
     int id = -1;
     shasta_status st = shasta_batch_add(s->batch, &j->ev.grid, j->ev.dx, j->ev.lambda, &j->ev.eos,
                                         f, j->ev.kind, SHASTA_MEM_DEVICE, &id);
-    if (st == SHASTA_EAGAIN) break;  // no contiguous room yet: retry next round
+    if (st == SHASTA_EAGAIN) break;  // no contiguous room yet: retry in a later worker round
     // the add has synchronised the compute stream: the staging is free
     cudaEventDestroy(j->in_ready);
     j->in_ready = nullptr;
@@ -372,7 +372,7 @@ bool admit(shasta_server* s) {
 // resident ones, and while those run copy the next queue heads in (first
 // come first served, while slots, pool room and input staging allow) and
 // admit them into the batch (stream-ordered after the steps, so they join
-// from the next round on; the admission's synchronisation also waits for
+// from the worker's next round on; the admission's synchronisation also waits for
 // the steps).
 void worker_main(shasta_server* s) {
   cudaSetDevice(s->o.device);

@@ -64,7 +64,7 @@ def sensitivity():
 
 
 @pytest.fixture(scope="module")
-def config2():
+def hot_spots_200():
     require_gpu()
     N = 200
     P = OR.params((N, N, N))
@@ -77,8 +77,8 @@ def config2():
 
 
 @pytest.mark.parametrize("precision", ["fp32", "mixed"])
-def test_config2_full_size_against_oracle(config2, precision):
-    U0, e75, ref, rp = config2
+def test_hot_spots_200_against_oracle(hot_spots_200, precision):
+    U0, e75, ref, rp = hot_spots_200
     N = 200
     with S.Solver((N, N, N), precision=precision) as s:  # autotune + graphs, as benched
         s.set_conserved(U0)
@@ -92,7 +92,7 @@ def test_config2_full_size_against_oracle(config2, precision):
     drift = [abs(float(np.sum(g)) - float(np.sum(u))) / float(np.abs(u).sum())
              for g, u in zip((got[0], got[4]), (U0[0], U0[4]))]
     envelope = sensitivity()["hot_spots_200_input_rounding"]["200"]
-    report(f"config2_{precision}", {"rel_l1_e_75": err75, "rel_l1_e_200": err200,
+    report(f"hot_spots_200_{precision}", {"rel_l1_e_75": err75, "rel_l1_e_200": err200,
                                     "fp64_input_rounding_envelope_200": envelope,
                                     "totals_gap_vs_oracle_200": gaps,
                                     "drift_E_R_vs_initial_200": drift})
@@ -102,7 +102,7 @@ def test_config2_full_size_against_oracle(config2, precision):
     assert max(drift) <= 1e-5, drift
 
 
-def test_config3_sampled_events_against_oracle():
+def test_batch_64_events_sampled_against_oracle():
     require_gpu()
     evs = W.batch_events(n_events=64, seed=3)
     total = sum(ev["N"] ** 3 for ev in evs)
@@ -125,14 +125,14 @@ def test_config3_sampled_events_against_oracle():
         ref = O.step(P, O.prim2cons(P, *inputs[i]), 100)
         rp = O.recover(P, ref)
         errs[i] = (rel_l1(got[i][0]["e"], rp["e"]), max(totals_gap(got[i][1], ref)))
-    report("config3_sampled_mixed", {f"event{i}_N{evs[i]['N']}": {"rel_l1_e": e, "totals_gap": t}
+    report("batch_64_events_sampled_mixed", {f"event{i}_N{evs[i]['N']}": {"rel_l1_e": e, "totals_gap": t}
                                      for i, (e, t) in errs.items()})
     for i, (e, t) in errs.items():
         assert e <= 1e-4 and t <= 1e-5, (i, e, t)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "mixed"])
-def test_config5_blast(precision):
+def test_blast_512(precision):
     require_gpu()
     # 512^3, 500 steps: conservation of E and R in the closed box
     N = 512
@@ -165,7 +165,7 @@ def test_config5_blast(precision):
     err125 = rel_l1(prim["e"], rp["e"])
     gaps = totals_gap(got, ref)
     envelope = sensitivity()["blast_128_delta_1e-6_vs_1e-10"]["125"]
-    report(f"config5_{precision}", {"drift_E_R_512": drift, "clamped_recoveries_512": clamps,
+    report(f"blast_512_{precision}", {"drift_E_R_512": drift, "clamped_recoveries_512": clamps,
                                     "rel_l1_e_128_50": err50, "rel_l1_e_128_125": err125,
                                     "fp64_clamp_margin_envelope_125": envelope,
                                     "totals_gap_128_125": gaps})

@@ -48,7 +48,7 @@ def fp64_check(shape, U0, nsteps, bc=OR.BC_REFLECT, eos=OR.EOS_IDEAL, tol=1e-12,
     return errs
 
 
-def test_fp64_config1_shock_tube():
+def test_fp64_shock_tube_64():
     """64^3 planar Riemann shock tube, FP64, 40 full split steps."""
     shape = (64, 64, 64)
     P = OR.params(shape)
@@ -96,7 +96,7 @@ def test_fp64_step_phase_and_resume():
 
 
 @pytest.mark.parametrize("precision", ["fp32", "mixed"])
-def test_fp32_config1_shock_tube(precision):
+def test_fp32_shock_tube_64(precision):
     shape = (64, 64, 64)
     O = oracle()
     P = OR.params(shape)
