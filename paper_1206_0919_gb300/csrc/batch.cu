@@ -67,12 +67,18 @@ struct shasta_batch {
   int nlive = 0;
   long long used = 0;
   EvDesc* d_desc = nullptr;
-  EvDesc* h_desc = nullptr;  // pinned
   unsigned long long* d_count = nullptr;  // per slot clamp counters; [max_events] check scratch
   int* d_plan = nullptr;
   size_t plan_cap = 0;  // ints
-  int* h_plan = nullptr;  // pinned
-  size_t h_plan_cap = 0;
+  // work-list uploads go through two pinned buffers used in turn, so that a
+  // new list is written while the previous copy may still be queued behind
+  // the steps (each buffer is reused only after its copy has run)
+  EvDesc* h_desc[2] = {};
+  int* h_plan[2] = {};
+  size_t h_plan_cap[2] = {};
+  cudaEvent_t up_done[2] = {};
+  bool up_pending[2] = {};
+  int up_next = 0;
   double* staging = nullptr;
   size_t staging_cells = 0;
   double* partials = nullptr;
@@ -239,17 +245,48 @@ int slots_in_use(const shasta_batch* b) {
   return n;
 }
 
-// Writes the descriptors of all slots in use (synchronous: the pinned copy
-// is reused).
-shasta_status upload_desc(shasta_batch* b) {
+// Uploads the descriptors of all slots in use and the work lists `host`
+// through the next pinned buffer pair; stream-ordered (the kernels already
+// queued read the previous lists), no host wait unless that buffer pair's
+// previous copy has not run yet.
+shasta_status upload_lists(shasta_batch* b, const std::vector<int>& host) {
+  const int i = b->up_next;
+  b->up_next ^= 1;
+  if (b->up_pending[i]) CK(cudaEventSynchronize(b->up_done[i]), "sync upload buffer");
+  b->up_pending[i] = false;
+  if (host.size() > b->plan_cap) {
+    // the device lists grow (rare): no queued kernel may still read them
+    CK(cudaStreamSynchronize(b->stream), "sync");
+    cudaFree(b->d_plan);
+    b->d_plan = nullptr;
+    b->plan_cap = 0;
+    size_t cap = std::max<size_t>(host.size() * 2, 4096);
+    CK(cudaMalloc((void**)&b->d_plan, cap * sizeof(int)), "cudaMalloc plan");
+    b->plan_cap = cap;
+  }
+  if (host.size() > b->h_plan_cap[i]) {
+    cudaFreeHost(b->h_plan[i]);
+    b->h_plan[i] = nullptr;
+    b->h_plan_cap[i] = 0;
+    size_t cap = std::max<size_t>(host.size() * 2, 4096);
+    CK(cudaMallocHost((void**)&b->h_plan[i], cap * sizeof(int)), "cudaMallocHost plan");
+    b->h_plan_cap[i] = cap;
+  }
   const int n = slots_in_use(b);
-  if (!n) return SHASTA_OK;
-  CK(cudaStreamSynchronize(b->stream), "sync");
-  for (int i = 0; i < n; ++i)
-    if (b->ev[i].live) b->h_desc[i] = desc_of(b, i);
-  CK(cudaMemcpyAsync(b->d_desc, b->h_desc, n * sizeof(EvDesc), cudaMemcpyHostToDevice, b->stream),
-     "upload descriptors");
-  CK(cudaStreamSynchronize(b->stream), "sync");
+  for (int k = 0; k < n; ++k)
+    if (b->ev[k].live) b->h_desc[i][k] = desc_of(b, k);
+  if (n)
+    CK(cudaMemcpyAsync(b->d_desc, b->h_desc[i], n * sizeof(EvDesc), cudaMemcpyHostToDevice,
+                       b->stream),
+       "upload descriptors");
+  if (!host.empty()) {
+    memcpy(b->h_plan[i], host.data(), host.size() * sizeof(int));
+    CK(cudaMemcpyAsync(b->d_plan, b->h_plan[i], host.size() * sizeof(int),
+                       cudaMemcpyHostToDevice, b->stream),
+       "upload plan");
+  }
+  CK(cudaEventRecord(b->up_done[i], b->stream), "record upload");
+  b->up_pending[i] = true;
   return SHASTA_OK;
 }
 
@@ -286,33 +323,6 @@ LaunchRec make_list(const shasta_batch* b, std::vector<int> ids, int axis, int e
   return L;
 }
 
-shasta_status upload_plan(shasta_batch* b, const std::vector<int>& host) {
-  if (host.empty()) return SHASTA_OK;
-  CK(cudaStreamSynchronize(b->stream), "sync");
-  if (host.size() > b->plan_cap) {
-    cudaFree(b->d_plan);
-    b->d_plan = nullptr;
-    b->plan_cap = 0;
-    size_t cap = std::max<size_t>(host.size() * 2, 4096);
-    CK(cudaMalloc((void**)&b->d_plan, cap * sizeof(int)), "cudaMalloc plan");
-    b->plan_cap = cap;
-  }
-  if (host.size() > b->h_plan_cap) {
-    cudaFreeHost(b->h_plan);
-    b->h_plan = nullptr;
-    b->h_plan_cap = 0;
-    size_t cap = std::max<size_t>(host.size() * 2, 4096);
-    CK(cudaMallocHost((void**)&b->h_plan, cap * sizeof(int)), "cudaMallocHost plan");
-    b->h_plan_cap = cap;
-  }
-  memcpy(b->h_plan, host.data(), host.size() * sizeof(int));
-  CK(cudaMemcpyAsync(b->d_plan, b->h_plan, host.size() * sizeof(int), cudaMemcpyHostToDevice,
-                     b->stream),
-     "upload plan");
-  CK(cudaStreamSynchronize(b->stream), "sync");
-  return SHASTA_OK;
-}
-
 void drop_graph(shasta_batch* b) {
   if (b->graph) cudaGraphExecDestroy(b->graph);
   b->graph = nullptr;
@@ -340,9 +350,7 @@ shasta_status build_plan(shasta_batch* b) {
           if (!groups[a][k].empty())
             b->plan[r][s].push_back(make_list(b, groups[a][k], a, k, host));
     }
-  shasta_status st = upload_desc(b);
-  if (st != SHASTA_OK) return st;
-  st = upload_plan(b, host);
+  shasta_status st = upload_lists(b, host);
   if (st != SHASTA_OK) return st;
   b->plan_base = b->bsteps;
   b->plan_valid = true;
@@ -421,7 +429,7 @@ shasta_status autotune(shasta_batch* b) {
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0), "cudaEventCreate");
   CK(cudaEventCreate(&e1), "cudaEventCreate");
-  shasta_status st = upload_desc(b);
+  shasta_status st = SHASTA_OK;
   const int n = slots_in_use(b);
   for (int a = 0; a < 3 && st == SHASTA_OK; ++a) {
     std::vector<int> host;
@@ -432,7 +440,7 @@ shasta_status autotune(shasta_batch* b) {
         if (b->ev[i].live && b->ev[i].eos.kind == k) ids.push_back(i);
       if (!ids.empty()) recs.push_back(make_list(b, ids, a, k, host));
     }
-    st = upload_plan(b, host);
+    st = upload_lists(b, host);
     if (st != SHASTA_OK) break;
     const long long total = total_positions(b, a);
     float best = 1e30f;
@@ -497,10 +505,13 @@ void release(shasta_batch* b) {
   for (Event& e : b->ev) cudaFree(e.frozen);
   cudaFree(b->pool);
   cudaFree(b->d_desc);
-  cudaFreeHost(b->h_desc);
   cudaFree(b->d_count);
   cudaFree(b->d_plan);
-  cudaFreeHost(b->h_plan);
+  for (int i = 0; i < 2; ++i) {
+    cudaFreeHost(b->h_desc[i]);
+    cudaFreeHost(b->h_plan[i]);
+    if (b->up_done[i]) cudaEventDestroy(b->up_done[i]);
+  }
   cudaFree(b->staging);
   cudaFree(b->partials);
   cudaFree(b->d_tot);
@@ -584,8 +595,11 @@ shasta_status shasta_batch_create(const shasta_batch_opts* o, shasta_batch** out
   }
   err = cudaMalloc((void**)&b->d_desc, (size_t)opts.max_events * sizeof(EvDesc));
   if (err != cudaSuccess) return bail(err, "cudaMalloc descriptors");
-  err = cudaMallocHost((void**)&b->h_desc, (size_t)opts.max_events * sizeof(EvDesc));
-  if (err != cudaSuccess) return bail(err, "cudaMallocHost descriptors");
+  for (int i = 0; i < 2 && err == cudaSuccess; ++i) {
+    err = cudaMallocHost((void**)&b->h_desc[i], (size_t)opts.max_events * sizeof(EvDesc));
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&b->up_done[i], cudaEventDisableTiming);
+  }
+  if (err != cudaSuccess) return bail(err, "pinned descriptors");
   err = cudaMalloc((void**)&b->d_count, ((size_t)opts.max_events + 1) * sizeof(unsigned long long));
   if (err != cudaSuccess) return bail(err, "cudaMalloc counters");
   err = cudaMemset(b->d_count, 0, ((size_t)opts.max_events + 1) * sizeof(unsigned long long));
@@ -624,9 +638,16 @@ shasta_status shasta_batch_destroy(shasta_batch* b) {
   return SHASTA_OK;
 }
 
-shasta_status shasta_batch_add(shasta_batch* b, const shasta_grid* g, double dx, double lambda,
-                               const shasta_eos* eos, const double* const fields[5], int kind,
-                               int mem, int* id) {
+}  // extern "C"
+
+namespace {
+
+// The add of shasta_batch_add.  check: scan the input (a host wait for the
+// verdict); wait: return only when the state is in place (the inputs may
+// then be reused at once).  Without either the add is only enqueued.
+shasta_status add_impl(shasta_batch* b, const shasta_grid* g, double dx, double lambda,
+                       const shasta_eos* eos, const double* const fields[5], int kind, int mem,
+                       int* id, bool check, bool wait) {
   if (!b) return SHASTA_EINVAL;
   if (!id) return fail(b, SHASTA_EINVAL, "id is NULL");
   *id = -1;
@@ -692,7 +713,7 @@ shasta_status shasta_batch_add(shasta_batch* b, const shasta_grid* g, double dx,
     }
   }
   unsigned long long* scratch = b->d_count + b->o.max_events;
-  if (b->o.check_input) {
+  if (check) {
     cudaError_t ce = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), b->stream);
     if (ce == cudaSuccess)
       ce = kind == SHASTA_STATE_PRIMITIVE ? launch_check_prims(d, ncell, scratch, b->stream)
@@ -721,7 +742,7 @@ shasta_status shasta_batch_add(shasta_batch* b, const shasta_grid* g, double dx,
     ce = launch_frozen_capture(v, ev.frozen, g->nx, g->ny, g->nz, 1, b->stream);
   if (ce == cudaSuccess)
     ce = cudaMemsetAsync(b->d_count + slot, 0, sizeof(unsigned long long), b->stream);
-  if (ce == cudaSuccess) ce = cudaStreamSynchronize(b->stream);
+  if (ce == cudaSuccess && (wait || mem == SHASTA_MEM_HOST)) ce = cudaStreamSynchronize(b->stream);
   if (ce != cudaSuccess) return undo(cuda_fail(b, ce, "set state"));
   ev.live = true;
   b->ev[slot] = ev;
@@ -733,11 +754,14 @@ shasta_status shasta_batch_add(shasta_batch* b, const shasta_grid* g, double dx,
   return SHASTA_OK;
 }
 
-shasta_status shasta_batch_remove(shasta_batch* b, int id) {
+// The remove of shasta_batch_remove; wait: first let the queued work finish.
+// Without it the cells are reused in stream order (later kernels on the
+// batch stream only); a frozen store is freed by cudaFree, which waits.
+shasta_status remove_impl(shasta_batch* b, int id, bool wait) {
   Event* e = find(b, id);
   if (!e) return b ? fail(b, SHASTA_ENOTFOUND, "unknown event id") : SHASTA_EINVAL;
   DeviceGuard dg(b->device);
-  CK(cudaStreamSynchronize(b->stream), "sync");
+  if (wait) CK(cudaStreamSynchronize(b->stream), "sync");
   cudaFree(e->frozen);
   b->cells.release(e->off, e->ncell);
   b->used -= e->ncell;
@@ -747,6 +771,48 @@ shasta_status shasta_batch_remove(shasta_batch* b, int id) {
   b->tuned = false;
   return SHASTA_OK;
 }
+
+}  // namespace
+
+namespace shasta {
+
+shasta_status batch_add_enqueue(shasta_batch* b, const shasta_grid* g, double dx, double lambda,
+                                const shasta_eos* eos, const double* const fields[5], int kind,
+                                int* id) {
+  return add_impl(b, g, dx, lambda, eos, fields, kind, SHASTA_MEM_DEVICE, id, false, false);
+}
+
+shasta_status batch_remove_enqueue(shasta_batch* b, int id) { return remove_impl(b, id, false); }
+
+shasta_status batch_extract_enqueue(shasta_batch* b, int id, double* const prims[6],
+                                    double* const cons[5], unsigned long long* counter) {
+  Event* e = find(b, id);
+  if (!e) return b ? fail(b, SHASTA_ENOTFOUND, "unknown event id") : SHASTA_EINVAL;
+  DeviceGuard dg(b->device);
+  const FieldView v = view_of(b, *e, b->cur);
+  bool any = false;
+  for (int k = 0; k < 6; ++k) any = any || prims[k];
+  if (any) CK(launch_recover(v, prims, e->ncell, 1, eos_params(b, *e), b->stream), "recover");
+  for (int k = 0; k < 5; ++k)
+    if (cons[k]) CK(launch_to_f64(v.p[k], v.s[k], cons[k], e->ncell, 1, b->stream), "convert out");
+  if (counter)
+    CK(cudaMemcpyAsync(counter, b->d_count + id, sizeof *counter, cudaMemcpyDeviceToDevice,
+                       b->stream),
+       "copy counter");
+  return SHASTA_OK;
+}
+
+}  // namespace shasta
+
+extern "C" {
+
+shasta_status shasta_batch_add(shasta_batch* b, const shasta_grid* g, double dx, double lambda,
+                               const shasta_eos* eos, const double* const fields[5], int kind,
+                               int mem, int* id) {
+  return add_impl(b, g, dx, lambda, eos, fields, kind, mem, id, b && b->o.check_input, true);
+}
+
+shasta_status shasta_batch_remove(shasta_batch* b, int id) { return remove_impl(b, id, true); }
 
 shasta_status shasta_batch_step(shasta_batch* b, int nsteps) {
   if (!b) return SHASTA_EINVAL;

@@ -18,9 +18,16 @@
 #include <vector>
 
 #include "../../include/shasta_serve.h"
+#include "batch_internal.h"
+#include "kernels.h"
 #include "range_alloc.h"
 
 using shasta::RangeAlloc;
+using shasta::batch_add_enqueue;
+using shasta::batch_extract_enqueue;
+using shasta::batch_remove_enqueue;
+using shasta::launch_check_cons;
+using shasta::launch_check_prims;
 
 namespace {
 
@@ -43,7 +50,9 @@ struct Job {
   double t_submit = 0, t_admit = 0, t_done = 0;
   int bid = -1;
   long long in_off = -1, out_off = -1, out_bytes = 0;
-  cudaEvent_t in_ready = nullptr;
+  cudaEvent_t in_ready = nullptr;   // inputs copied in and scanned
+  cudaEvent_t out_ready = nullptr;  // results in output staging
+  int chk = -1;                     // input-scan slot while staged
   int64_t steps_left = 0, steps = 0, clamps = 0;
 };
 
@@ -136,6 +145,16 @@ struct shasta_server {
   char* out_base = nullptr;
   RangeAlloc in_arena{256}, out_arena{256};
   Bounce bounce;  // the deliverer's
+  // input scans of staged events: device counters and their pinned copies
+  unsigned long long* d_chk = nullptr;
+  unsigned long long* h_chk = nullptr;
+  bool chk_used[kMaxStaged] = {};
+  // the worker runs at most two iterations ahead of the device: iteration i
+  // waits for iteration i-2 (same parity), then releases the input staging
+  // of the events that iteration admitted
+  cudaEvent_t iter_done[2] = {};
+  bool iter_pending[2] = {};
+  std::vector<JobP> releasing[2];
   long long pool_cells = 0;
   std::chrono::steady_clock::time_point t0;
   std::mutex mu;  // guards the queue, the job table, out_arena, deliver and the counters
@@ -224,7 +243,8 @@ bool cuda_ok(shasta_server* s, cudaError_t e, const char* where) {
 }
 
 // The deliverer thread: copies results from output staging into the
-// callers' buffers while the worker keeps the batch stepping.
+// callers' buffers (once the extraction queued by the worker has run) while
+// the worker keeps the batch stepping.
 void deliverer_main(shasta_server* s) {
   cudaSetDevice(s->o.device);
   for (;;) {
@@ -250,7 +270,11 @@ void deliverer_main(shasta_server* s) {
       if (j->ev.out_prims[i]) field(j->ev.out_prims[i]);
     for (int i = 0; i < 5; ++i)
       if (j->ev.out_cons[i]) field(j->ev.out_cons[i]);
-    cudaError_t e = bounce_d2h(s->bounce, pcs, s->copy_out);
+    pcs.push_back(Piece{(char*)&j->clamps, base + k * bytes, sizeof(int64_t)});  // clamp counter
+    cudaError_t e = cudaStreamWaitEvent(s->copy_out, j->out_ready, 0);
+    if (e == cudaSuccess) e = bounce_d2h(s->bounce, pcs, s->copy_out);
+    cudaEventDestroy(j->out_ready);
+    j->out_ready = nullptr;
     {
       std::lock_guard<std::mutex> lk(s->mu);
       s->out_arena.release(j->out_off, j->out_bytes);
@@ -265,8 +289,9 @@ void deliverer_main(shasta_server* s) {
   }
 }
 
-// Takes finished jobs out of the batch: results into output staging, from
-// where the deliverer copies them to the callers.
+// Events whose steps are all queued: their results (and clamp counter) are
+// queued into output staging behind the steps, the event leaves the batch
+// (its cells are reused only by later work), and the deliverer takes over.
 bool harvest(shasta_server* s) {
   std::vector<JobP> keep;
   for (const JobP& j : s->resident) {
@@ -274,14 +299,9 @@ bool harvest(shasta_server* s) {
       keep.push_back(j);
       continue;
     }
-    int64_t c = 0;
-    shasta_status st = shasta_batch_counters(s->batch, j->bid, &c);
-    if (st != SHASTA_OK) return stop_all(s, batch_msg(s, "counters")), false;
-    j->clamps = c;
     const int nout = n_outputs(j->ev);
-    j->out_bytes = (long long)nout * j->ncell * (long long)sizeof(double);
-    j->out_off = -1;
-    if (nout) {
+    j->out_bytes = ((long long)nout * j->ncell + 1) * (long long)sizeof(double);
+    {
       // room in output staging: every job's outputs fit it, so waiting for
       // the deliverer to free some always ends
       std::unique_lock<std::mutex> lk(s->mu);
@@ -293,60 +313,133 @@ bool harvest(shasta_server* s) {
     double* pr[6] = {};
     double* cs[5] = {};
     int k = 0;
-    double* base = (double*)(s->out_base + (j->out_off > 0 ? j->out_off : 0));
-    bool any_p = false, any_c = false;
+    double* base = (double*)(s->out_base + j->out_off);
     for (int i = 0; i < 6; ++i)
-      if (j->ev.out_prims[i]) {
-        pr[i] = base + (size_t)(k++) * j->ncell;
-        any_p = true;
-      }
+      if (j->ev.out_prims[i]) pr[i] = base + (size_t)(k++) * j->ncell;
     for (int i = 0; i < 5; ++i)
-      if (j->ev.out_cons[i]) {
-        cs[i] = base + (size_t)(k++) * j->ncell;
-        any_c = true;
-      }
-    if (any_p && shasta_batch_get_primitives(s->batch, j->bid, pr, SHASTA_MEM_DEVICE) != SHASTA_OK)
+      if (j->ev.out_cons[i]) cs[i] = base + (size_t)(k++) * j->ncell;
+    unsigned long long* cnt = (unsigned long long*)(base + (size_t)k * j->ncell);
+    if (batch_extract_enqueue(s->batch, j->bid, pr, cs, cnt) != SHASTA_OK)
       return stop_all(s, batch_msg(s, "results")), false;
-    if (any_c && shasta_batch_get_conserved(s->batch, j->bid, cs, SHASTA_MEM_DEVICE) != SHASTA_OK)
-      return stop_all(s, batch_msg(s, "results")), false;
-    if (shasta_batch_remove(s->batch, j->bid) != SHASTA_OK) return stop_all(s, batch_msg(s, "remove")), false;
+    if (!cuda_ok(s, cudaEventCreateWithFlags(&j->out_ready, cudaEventDisableTiming), "event") ||
+        !cuda_ok(s, cudaEventRecord(j->out_ready, s->compute), "event"))
+      return false;
+    if (batch_remove_enqueue(s->batch, j->bid) != SHASTA_OK)
+      return stop_all(s, batch_msg(s, "remove")), false;
     j->bid = -1;
-    if (j->out_off >= 0) {
-      std::lock_guard<std::mutex> lk(s->mu);
-      j->st = J_OUT;
-      s->deliver.push_back(j);
-      s->cv_deliver.notify_one();
-    } else {
-      finish(s, j, SHASTA_OK);
-    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    j->st = J_OUT;
+    s->deliver.push_back(j);
+    s->cv_deliver.notify_one();
   }
   s->resident.swap(keep);
   return true;
 }
 
-// Admits staged jobs into the batch, in order, while the pool has room;
-// only at phase 0 of the resident events (so that they stay in step).
-bool admit(shasta_server* s) {
+void release_input(shasta_server* s, const JobP& j) {
+  if (j->in_ready) cudaEventDestroy(j->in_ready);
+  j->in_ready = nullptr;
+  if (j->chk >= 0) s->chk_used[j->chk] = false;
+  j->chk = -1;
+  if (j->in_off >= 0) s->in_arena.release(j->in_off, 5 * j->ncell * (long long)sizeof(double));
+  j->in_off = -1;
+  std::vector<double>().swap(j->in);
+}
+
+// Copies the next queue heads into input staging on the copy stream (first
+// come first served, while slots, pool room and input staging allow) and
+// scans them there for unphysical values.
+bool stage(shasta_server* s) {
+  std::vector<JobP> to_stage;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    // pool room: the largest free run less what staged events will take
+    int64_t info[7] = {};
+    shasta_batch_info(s->batch, info);
+    long long room = info[3];
+    for (const JobP& j : s->staged) room -= pool_need(j->ncell);
+    int slots = s->o.max_resident - (int)s->resident.size() - (int)s->staged.size();
+    while (!s->queue.empty() && (int)(s->staged.size() + to_stage.size()) < kMaxStaged &&
+           slots > 0) {
+      const JobP& j = s->queue.front();
+      if (pool_need(j->ncell) > room) break;
+      const long long off = s->in_arena.alloc(5 * j->ncell * (long long)sizeof(double));
+      if (off < 0) break;
+      j->in_off = off;
+      j->st = J_STAGED;
+      room -= pool_need(j->ncell);
+      --slots;
+      to_stage.push_back(j);
+      s->queue.pop_front();
+    }
+  }
+  for (const JobP& j : to_stage) {
+    // a slot per staged job (at most kMaxStaged; freed when admission reads it)
+    int c = 0;
+    while (c < kMaxStaged && s->chk_used[c]) ++c;
+    if (c == kMaxStaged) return stop_all(s, "no input-scan slot"), false;
+    s->chk_used[c] = true;
+    j->chk = c;
+    double* d = (double*)(s->in_base + j->in_off);
+    const double* f[5];
+    for (int k = 0; k < 5; ++k) f[k] = d + (size_t)k * j->ncell;
+    cudaError_t e = cudaEventCreateWithFlags(&j->in_ready, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d, j->in.data(), 5 * j->ncell * sizeof(double), cudaMemcpyHostToDevice,
+                          s->copy);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_chk + c, 0, sizeof(unsigned long long), s->copy);
+    if (e == cudaSuccess)
+      e = j->ev.kind == SHASTA_STATE_PRIMITIVE
+              ? launch_check_prims(f, (size_t)j->ncell, s->d_chk + c, s->copy)
+              : launch_check_cons(f, (size_t)j->ncell, s->d_chk + c, s->copy);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s->h_chk + c, s->d_chk + c, sizeof(unsigned long long),
+                          cudaMemcpyDeviceToHost, s->copy);
+    if (e == cudaSuccess) e = cudaEventRecord(j->in_ready, s->copy);
+    s->staged.push_back(j);
+    if (!cuda_ok(s, e, "copy in")) return false;
+  }
+  return true;
+}
+
+// Admits staged jobs whose inputs are in and scanned, in order, while the
+// pool has room; only at phase 0 of the resident events (so that they stay
+// in step).  The conversion into the pool is queued on the batch stream;
+// input staging is released once the iteration's work has run (`p`).
+bool admit(shasta_server* s, int p) {
   if (!s->resident.empty() && s->resident.front()->steps % 6 != 0) return true;
   size_t i = 0;
   for (; i < s->staged.size(); ++i) {
     const JobP& j = s->staged[i];
+    const cudaError_t q = cudaEventQuery(j->in_ready);
+    if (q == cudaErrorNotReady) break;  // later, in order
+    if (!cuda_ok(s, q, "copy in")) return false;
+    const unsigned long long bad = s->h_chk[j->chk];
+    s->chk_used[j->chk] = false;  // the scan's result is read
+    j->chk = -1;
+    if (bad) {
+      char m[160];
+      snprintf(m, sizeof m, "%llu cells are not physical (non-finite, %s)", bad,
+               j->ev.kind == SHASTA_STATE_PRIMITIVE ? "e < 0, n < 0 or |v| >= 1" : "E < 0 or |M| >= E");
+      release_input(s, j);
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->err = m;
+      }
+      finish(s, j, SHASTA_EUNPHYSICAL);
+      continue;
+    }
     if (!cuda_ok(s, cudaStreamWaitEvent(s->compute, j->in_ready, 0), "wait input")) return false;
     const double* base = (const double*)(s->in_base + j->in_off);
     const double* f[5];
     for (int k = 0; k < 5; ++k) f[k] = base + (size_t)k * j->ncell;
     int id = -1;
-    shasta_status st = shasta_batch_add(s->batch, &j->ev.grid, j->ev.dx, j->ev.lambda, &j->ev.eos,
-                                        f, j->ev.kind, SHASTA_MEM_DEVICE, &id);
+    shasta_status st = batch_add_enqueue(s->batch, &j->ev.grid, j->ev.dx, j->ev.lambda, &j->ev.eos,
+                                         f, j->ev.kind, &id);
     if (st == SHASTA_EAGAIN) break;  // no contiguous room yet: retry in a later worker round
-    // the add has synchronised the compute stream: the staging is free
-    cudaEventDestroy(j->in_ready);
-    j->in_ready = nullptr;
-    s->in_arena.release(j->in_off, 5 * j->ncell * (long long)sizeof(double));
-    j->in_off = -1;
-    std::vector<double>().swap(j->in);
     if (st == SHASTA_ECUDA || st == SHASTA_ENOMEM) return stop_all(s, batch_msg(s, "admit")), false;
     if (st != SHASTA_OK) {
+      release_input(s, j);
       {
         std::lock_guard<std::mutex> lk(s->mu);
         s->err = shasta_batch_last_error(s->batch);
@@ -354,6 +447,7 @@ bool admit(shasta_server* s) {
       finish(s, j, st);
       continue;
     }
+    s->releasing[p].push_back(j);
     j->bid = id;
     j->steps_left = j->ev.nsteps;
     {
@@ -368,12 +462,12 @@ bool admit(shasta_server* s) {
   return true;
 }
 
-// One round: take finished events out, enqueue the next steps of the
-// resident ones, and while those run copy the next queue heads in (first
-// come first served, while slots, pool room and input staging allow) and
-// admit them into the batch (stream-ordered after the steps, so they join
-// from the worker's next round on; the admission's synchronisation also waits for
-// the steps).
+// The worker: iterations of (wait for the iteration before last, queue the
+// next steps of the resident events, queue the results of the events that
+// are through, copy and scan the next queue heads, admit the staged ones).
+// Everything it queues on the device is stream-ordered, so the device
+// always has the previous iteration's steps to run while the worker
+// prepares the next one.
 void worker_main(shasta_server* s) {
   cudaSetDevice(s->o.device);
   double tp[7] = {};  // [4] (copy out) is kept by the deliverer
@@ -383,21 +477,29 @@ void worker_main(shasta_server* s) {
     tp[k] += t - mark;
     mark = t;
   };
-  for (;;) {
+  for (int64_t iter = 0;; ++iter) {
     {
       std::unique_lock<std::mutex> lk(s->mu);
       for (int k = 0; k < 7; ++k)
         if (k != 4) s->t_phase[k] = tp[k];
       if (s->stop || s->fatal != SHASTA_OK) break;
-      if (s->queue.empty() && s->staged.empty() && s->resident.empty()) {
+      if (s->queue.empty() && s->staged.empty() && s->resident.empty() &&
+          !s->iter_pending[0] && !s->iter_pending[1]) {
         s->cv_work.wait_for(lk, std::chrono::milliseconds(20));
         lk.unlock();
         lap(6);
         continue;
       }
     }
-    if (!harvest(s)) break;
-    lap(2);
+    const int p = (int)(iter & 1);
+    if (s->iter_pending[p]) {
+      if (!cuda_ok(s, cudaEventSynchronize(s->iter_done[p]), "wait")) break;
+      s->iter_pending[p] = false;
+      for (const JobP& j : s->releasing[p]) release_input(s, j);
+      s->releasing[p].clear();
+    }
+    lap(5);
+    bool queued = false;
     if (!s->resident.empty()) {
       // every resident event is at the same phase of the six-step axis
       // table (events join only at phase 0), so each sweep slot sweeps one
@@ -413,6 +515,7 @@ void worker_main(shasta_server* s) {
         j->steps_left -= k;
         j->steps += k;
       }
+      queued = queued || k > 0;
       int64_t info[7] = {};
       shasta_batch_info(s->batch, info);
       std::lock_guard<std::mutex> lk(s->mu);
@@ -420,50 +523,25 @@ void worker_main(shasta_server* s) {
       s->sweep_launches = info[6];
     }
     lap(3);
-    // copy the next events in while the steps run
-    std::vector<JobP> to_stage;
-    {
-      std::lock_guard<std::mutex> lk(s->mu);
-      // pool room: the largest free run less what staged events will take
-      int64_t info[7] = {};
-      shasta_batch_info(s->batch, info);
-      long long room = info[3];
-      for (const JobP& j : s->staged) room -= pool_need(j->ncell);
-      int slots = s->o.max_resident - (int)s->resident.size() - (int)s->staged.size();
-      while (!s->queue.empty() && (int)(s->staged.size() + to_stage.size()) < kMaxStaged &&
-             slots > 0) {
-        const JobP& j = s->queue.front();
-        if (pool_need(j->ncell) > room) break;
-        const long long off = s->in_arena.alloc(5 * j->ncell * (long long)sizeof(double));
-        if (off < 0) break;
-        j->in_off = off;
-        j->st = J_STAGED;
-        room -= pool_need(j->ncell);
-        --slots;
-        to_stage.push_back(j);
-        s->queue.pop_front();
-      }
-    }
-    bool ok = true;
-    for (const JobP& j : to_stage) {
-      double* d = (double*)(s->in_base + j->in_off);
-      ok = cuda_ok(s, cudaEventCreateWithFlags(&j->in_ready, cudaEventDisableTiming), "event") &&
-           cuda_ok(s, cudaMemcpyAsync(d, j->in.data(), 5 * j->ncell * sizeof(double),
-                                      cudaMemcpyHostToDevice, s->copy),
-                   "copy in") &&
-           cuda_ok(s, cudaEventRecord(j->in_ready, s->copy), "event");
-      if (!ok) break;
-      s->staged.push_back(j);
-    }
-    if (!ok) break;
+    const size_t out0 = s->resident.size();
+    if (!harvest(s)) break;
+    queued = queued || s->resident.size() != out0;
+    lap(2);
+    if (!stage(s)) break;
     lap(0);
-    if (!admit(s)) break;
+    const size_t admitted0 = s->releasing[p].size();
+    if (!admit(s, p)) break;
     lap(1);
-    if (shasta_batch_sync(s->batch) != SHASTA_OK) {
-      stop_all(s, batch_msg(s, "sync"));
-      break;
+    const bool admitted = s->releasing[p].size() != admitted0;
+    if (queued || admitted) {
+      if (!cuda_ok(s, cudaEventRecord(s->iter_done[p], s->compute), "record")) break;
+      s->iter_pending[p] = true;
     }
-    lap(5);
+    if (s->resident.empty() && !admitted && !s->staged.empty()) {
+      // nothing to run: wait for the oldest copy in flight instead of spinning
+      if (!cuda_ok(s, cudaEventSynchronize(s->staged.front()->in_ready), "wait input")) break;
+      lap(6);
+    }
   }
 }
 
@@ -478,12 +556,21 @@ void release(shasta_server* s) {
   s->cv_space.notify_all();
   if (s->worker.joinable()) s->worker.join();
   if (s->deliverer.joinable()) s->deliverer.join();
-  if (s->batch) shasta_batch_destroy(s->batch);
+  if (s->batch) shasta_batch_destroy(s->batch);  // waits for the batch stream
   if (s->copy) cudaStreamSynchronize(s->copy);
   if (s->copy_out) cudaStreamSynchronize(s->copy_out);
   for (const JobP& j : s->staged)
     if (j->in_ready) cudaEventDestroy(j->in_ready);
+  for (int p = 0; p < 2; ++p) {
+    for (const JobP& j : s->releasing[p])
+      if (j->in_ready) cudaEventDestroy(j->in_ready);
+    if (s->iter_done[p]) cudaEventDestroy(s->iter_done[p]);
+  }
+  for (const JobP& j : s->deliver)
+    if (j->out_ready) cudaEventDestroy(j->out_ready);
   cudaFree(s->staging);
+  cudaFree(s->d_chk);
+  cudaFreeHost(s->h_chk);
   bounce_free(s->bounce);
   if (s->compute) cudaStreamDestroy(s->compute);
   if (s->copy) cudaStreamDestroy(s->copy);
@@ -553,6 +640,10 @@ shasta_status shasta_server_create(const shasta_server_opts* o, shasta_server** 
     return bail(ce == cudaErrorMemoryAllocation ? SHASTA_ENOMEM : SHASTA_ECUDA,
                 std::string("staging: ") + cudaGetErrorString(ce));
   ce = bounce_init(s->bounce);
+  if (ce == cudaSuccess) ce = cudaMalloc((void**)&s->d_chk, kMaxStaged * sizeof(unsigned long long));
+  if (ce == cudaSuccess) ce = cudaMallocHost((void**)&s->h_chk, kMaxStaged * sizeof(unsigned long long));
+  for (int p = 0; p < 2 && ce == cudaSuccess; ++p)
+    ce = cudaEventCreateWithFlags(&s->iter_done[p], cudaEventDisableTiming);
   if (ce != cudaSuccess)
     return bail(SHASTA_ENOMEM, std::string("pinned host buffers: ") + cudaGetErrorString(ce));
   s->in_base = (char*)s->staging;
