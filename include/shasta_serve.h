@@ -3,17 +3,20 @@
  *
  * Events of different grid sizes arrive as they come (shasta_submit never
  * blocks).  A worker thread of the server admits them into one resident
- * batch (shasta_batch.h) at step boundaries, first come first served, as
- * soon as a slot, contiguous room in the state pool and staging memory are
- * free: admission is by device-memory footprint (40 bytes per cell of state
+ * batch (shasta_batch.h) at the boundaries of the resident events' six-step
+ * axis cycle (Sec. 3.1.4), first come first served, as soon as a slot,
+ * contiguous room in the state pool and staging memory are free and their
+ * input has been copied in and scanned for unphysical values: admission is
+ * by device-memory footprint (40 bytes per cell of state
  * plus 40 bytes per cell of input staging while it is copied in and 8 per
  * cell and output field while the results are copied out; staging_bytes is
  * split evenly between input and output staging).  All resident events
  * advance together in the batched launches; an event leaves the batch after
  * its own number of steps, its results are copied into the caller's buffers
  * and its room goes to the next event in the queue.  Input copies of queued
- * events and output copies of finished ones run on a copy stream while the
- * resident events compute.
+ * events and output copies of finished ones run on copy streams while the
+ * resident events compute; the worker only queues work on the device, at
+ * most two rounds ahead of it.
  *
  * Each event advances exactly as it would alone (bit for bit: the batched
  * launch runs the single-event arithmetic), whatever else is resident.
