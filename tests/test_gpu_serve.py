@@ -166,3 +166,36 @@ def test_drain_times_out_then_completes():
             srv.drain(120.0)
             r = srv.poll(t)
         assert r["steps"] == 400
+
+
+def test_conserved_inputs_and_their_scan():
+    """Events given as conserved fields: a valid one gives the single
+    context's result bit for bit and reports the clamp counter; one with a
+    cell where |M| >= E is refused (EUNPHYSICAL) by the scan on the copy
+    stream while the other events keep running; an event without result
+    buffers still finishes."""
+    require_gpu()
+    from oracle import oracle as OR
+    from gpu_util import oracle
+    shape = (24, 20, 16)
+    P = OR.params(shape)
+    U = oracle().prim2cons(P, *prims_of(shape, 12, "ideal"))
+    bad = [u.copy() for u in U]
+    bad[1][2, 3, 4] = 1.5 * bad[0][2, 3, 4]  # |M| > E
+    with S.Server(1 << 30) as srv:
+        tg = srv.submit(shape, U, 11, kind="conserved", cons_out=True)
+        tb = srv.submit(shape, bad, 11, kind="conserved")
+        tn = srv.submit(shape, U, 5, kind="conserved", prims_out=False)
+        srv.drain(120.0)
+        good = srv.poll(tg)
+        with pytest.raises(S.ShastaError) as ei:
+            srv.poll(tb)
+        assert ei.value.status == S.EUNPHYSICAL
+        assert srv.poll(tn)["steps"] == 5
+    with S.Solver(shape) as s:
+        s.set_conserved(U)
+        s.step(11)
+        ref = s.get_conserved()
+        clamps = s.counters()
+    assert all(np.array_equal(r, g) for r, g in zip(ref, good["cons"]))
+    assert good["clamp_count"] == clamps
