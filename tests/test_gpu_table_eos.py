@@ -86,3 +86,19 @@ def test_fp32_ideal_table_follows_closed_form():
         ideal = s.get_primitives()
     _, prim, _ = run(shape, U0, 20, "fp32", IDEAL)
     assert rel_l1(prim["e"], ideal["e"]) <= 1e-4
+
+
+def test_batches_and_servers_refuse_a_table():
+    """Batches and the serving loop take closed-form EoS only: an event with
+    a tabulated EoS is refused with EINVAL."""
+    require_gpu()
+    shape = (8, 8, 8)
+    pr = W.hot_spots(shape=shape, seed=1, n_spots=2).as_list()
+    with S.Batch(4096, max_events=4) as b:
+        with pytest.raises(S.ShastaError) as ei:
+            b.add_primitives(shape, pr, eos=S.EOS_TABLE)
+        assert ei.value.status == S.EINVAL
+    with S.Server(1 << 28) as srv:
+        with pytest.raises(S.ShastaError) as ei:
+            srv.submit(shape, pr, 2, eos=S.EOS_TABLE)
+        assert ei.value.status == S.EINVAL
