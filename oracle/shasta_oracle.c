@@ -30,7 +30,15 @@
  *  - the bag EoS gap (no root on either branch) resolves to the mixed-phase
  *    point e = e_c;
  *  - the ghost cells of the half-step state are filled by the boundary rule
- *    after the half step (reflecting, periodic) or keep their frozen values.
+ *    after the half step (reflecting, periodic) or keep their frozen values;
+ *  - a tabulated EoS is linear between its nodes and continued from its last
+ *    interval; its fixed-point iteration starts from v = M/(E + p(E)) and
+ *    stops at a change of at most 1e-14.
+ *
+ * Parity unpinned: the clamp margin delta, the bag-EoS gap rule and the
+ * choice of a half step with antidiffusion are readings the paper does not
+ * fix; no pin can confirm them, and the tests compare the GPU with this
+ * oracle under the same readings.
  */
 #include "shasta_oracle.h"
 
