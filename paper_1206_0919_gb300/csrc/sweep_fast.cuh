@@ -824,7 +824,18 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, i
         const float* ring = x_slot(fl >> 3);
         const int r0 = lane >> 3, pc = lane & 7;
         const int pos = fl + pc;
-        if (pos < avail) {
+        if (pos < avail && (long long)(g + 1) * LANES <= G.plane()) {
+          // a full line group: every row exists
+          const unsigned sb4 = 4u * (unsigned)G.sb();
+          unsigned c = (unsigned)G.off() + (unsigned)(g * LANES + r0) * (unsigned)G.sb() + (unsigned)pos;
+#pragma unroll 4
+          for (int k = 0; k < 8; ++k, c += sb4) {
+            const int row = r0 + 4 * k;
+            *reinterpret_cast<float4*>(P.qout + 4 * (size_t)c) =
+                *reinterpret_cast<const float4*>(ring + row * XQSTR + pc * 4);
+            P.rout[c] = ring[XQ + row * XRSTR + pc];
+          }
+        } else if (pos < avail) {
 #pragma unroll 2
           for (int k = 0; k < 8; ++k) {
             const int row = r0 + 4 * k;
