@@ -9,7 +9,8 @@
  * input has been copied in and scanned for unphysical values: admission is
  * by device-memory footprint (40 bytes per cell of state
  * plus 40 bytes per cell of input staging while it is copied in and 8 per
- * cell and output field while the results are copied out; staging_bytes is
+ * cell and output field, plus 8 for the clamp counter, while the results
+ * are copied out; staging_bytes is
  * split evenly between input and output staging).  All resident events
  * advance together in the batched launches; an event leaves the batch after
  * its own number of steps, its results are copied into the caller's buffers

@@ -701,7 +701,7 @@ shasta_status shasta_submit(shasta_server* s, const shasta_event* ev, uint64_t* 
   const long long ncell = (long long)g.nx * g.ny * g.nz;
   if (pool_need(ncell) > s->pool_cells) return fail(s, SHASTA_EINVAL, "grid larger than the state pool");
   if (5 * ncell * (long long)sizeof(double) > s->in_cap ||
-      n_outputs(*ev) * ncell * (long long)sizeof(double) > s->out_cap)
+      (n_outputs(*ev) * ncell + 1) * (long long)sizeof(double) > s->out_cap)  // + clamp counter
     return fail(s, SHASTA_EINVAL, "grid larger than the staging memory");
   {
     std::lock_guard<std::mutex> lk(s->mu);
