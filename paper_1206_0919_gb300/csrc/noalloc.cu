@@ -11,8 +11,6 @@
 // cudaMalloc, cudaFree or any routine that allocates device memory.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "../../include/shasta.h"
 #include "kernels.h"
 
@@ -29,23 +27,18 @@ static_assert((size_t)kMaxBlocks * kCellsPerBlock == SHASTA_TOTALS_NOALLOC_MAX_C
 
 static __device__ __align__(256) double g_totals_scratch[5 * kMaxBlocks];
 
-// Device address of g_totals_scratch per device ordinal, looked up once.
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-double* g_scratch_addr[kMaxDevices] = {};
-
+// Device address of g_totals_scratch on the current device.  It is looked up
+// on every call rather than cached: after a device reset (or any teardown of
+// the primary context) the runtime loads this module again, possibly at
+// another address, and a cached pointer would then be stale.  The lookup is
+// a table search in the runtime and allocates nothing.
 shasta_status scratch_for_current_device(double** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return SHASTA_ECUDA;
-  if (dev < 0 || dev >= kMaxDevices) return SHASTA_EINVAL;
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
-    double* p = nullptr;
-    if (cudaGetSymbolAddress((void**)&p, g_totals_scratch) != cudaSuccess || !p)
-      return SHASTA_ECUDA;
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
+  double* p = nullptr;
+  if (cudaGetSymbolAddress((void**)&p, g_totals_scratch) != cudaSuccess || !p)
+    return SHASTA_ECUDA;
+  *out = p;
   return SHASTA_OK;
 }
 

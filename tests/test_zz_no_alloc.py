@@ -45,13 +45,15 @@ def test_size_limit_rejected_before_any_gpu_work():
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_noalloc_totals_match_shasta_totals_twice(precision):
     """First call on a 64x60x56 grid (27 blocks of partials, the last one
-    ragged), second call on a 24x20x16 grid (one block): the second must not
-    pick up partials the first left in the shared array."""
+    ragged), second call on a 40x36x32 grid (6 blocks, the last one ragged):
+    the first call leaves partials of other data in every slot the second
+    reads, so a second call that read a wrong block count or stride, or a
+    slot it did not write, would pick them up and fail."""
     require_gpu()
     import torch
     dev = torch.device("cuda:0")
     out = torch.full((5,), float("nan"), dtype=torch.float64, device=dev)
-    for shape, seed, steps in (((64, 60, 56), 11, 3), ((24, 20, 16), 12, 2)):
+    for shape, seed, steps in (((64, 60, 56), 11, 3), ((40, 36, 32), 12, 2)):
         prims = W.hot_spots(seed=seed, n_spots=6, radial_flow=0.3, shape=shape)
         with S.Solver(shape, precision=precision) as s:
             s.set_primitives(*prims.as_list())
