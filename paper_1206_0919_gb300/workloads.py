@@ -183,3 +183,26 @@ def serving_stream(n_events=2000, rate_hz=200.0, seed=4, sizes=SERVE_SIZES,
         out.append(dict(t_arrival=t, N=N, n_spots=k, seed=1000 * seed + i,
                         eos="ideal" if i % 2 == 0 else "bag", steps=steps))
     return out
+
+
+# ------------------------------------------------- single-precision inputs ----
+
+def rounded_to_single(fields):
+    """Each array rounded to the nearest float32 and widened back to float64:
+    the values a single-precision state holds for these inputs."""
+    return [np.asarray(a, dtype=np.float64).astype(np.float32).astype(np.float64) for a in fields]
+
+
+def ulp_flips(fields, seed):
+    """Each array rounded to float32, then every nonzero value moved one
+    float32 ulp up or down at random (seeded; zeros stay zero), widened back
+    to float64: seeded rounding-size perturbations of a single-precision
+    input."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for a in fields:
+        f = np.asarray(a, dtype=np.float64).astype(np.float32)
+        up = rng.integers(0, 2, size=f.shape).astype(bool)
+        g = np.where(up, np.nextafter(f, np.float32(np.inf)), np.nextafter(f, np.float32(-np.inf)))
+        out.append(np.where(f == 0, f, g).astype(np.float64))
+    return out
