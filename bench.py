@@ -4,12 +4,17 @@
 Workload: a 200^3 event of Gaussian hot spots (30 spots, centres in the
 central half of the box, sigma 3-8 cells, amplitudes log-uniform in [0.1, 10]
 on a 1e-6 background, n = e^(3/4), v = 0), ideal gas p = e/3, lambda = 0.4,
-reflecting walls, FP32 state.  One benchmark step is one full x/y/z split
-SHASTA step (three fused sweep kernels) of that state, resident in HBM.
+reflecting walls, FP32 state.  One benchmark step is one event of that
+workload: its initial state set from device-resident arrays through the C
+ABI, then its 200 full x/y/z split SHASTA steps (three fused sweep kernels
+each), the state resident in HBM.
 
 Prints one JSON line (rank 0).  value = cell-updates per second of the whole
 job (N replicas under torchrun: each rank advances its own event; there is
-no data-path collective, scaling is weak).
+no data-path collective, scaling is weak).  The same line carries the
+batched workload (64 uneven events in one batch, "batch64") and the serving
+loop (short Poisson streams at 60 and 200 events/s, "serve") as objects of
+their own; --no-legs leaves them out.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -42,14 +47,17 @@ FALLBACK_HBM_GBS = 6800.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=20,
+                    help="timed steps; the headline workload's step is one 200-step event")
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "mixed", "fp64"], default="fp32")
     ap.add_argument("--grid", type=int, default=N_GRID)
     ap.add_argument("--e2e-events", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="headline line without the batched and serving legs")
     ap.add_argument("--mode", choices=["full", "kernels"], default="full",
                     help="kernels: only warmup + K steps (for profiler captures)")
     ap.add_argument("--workload", choices=["single", "batch64", "serve", "tube64", "blast512", "ball200",
@@ -188,6 +196,65 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def workload_seed(rank):
+    """Seed of the event rank `rank` advances (each replica its own hot spots)."""
+    return 2 + 1000 * rank
+
+
+class Ranks:
+    """Process group of a replica run: one rank per GPU under torchrun, each
+    advancing its own events.  The group carries only the barriers around
+    the timed region, the maximum over ranks of the timings and the gathers
+    of summary numbers; there is no data-path collective.  backend "nccl"
+    on GPUs; "gloo" (CPU tensors) serves the host-side tests."""
+
+    def __init__(self, backend="nccl", device=None):
+        self.rank, self.world, self.local = dist_env()
+        self.dist = None
+        self.device = device
+        if self.world > 1:
+            import torch.distributed as dist
+            kw = {"device_id": device} if backend == "nccl" and device is not None else {}
+            dist.init_process_group(backend, **kw)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def _reduce(self, x, op):
+        if self.dist is None:
+            return float(x)
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64,
+                         device=self.device if self.device is not None else "cpu")
+        self.dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    def max(self, x):
+        """Maximum over ranks (timings: the job ends with its slowest rank)."""
+        return self._reduce(x, None if self.dist is None else self.dist.ReduceOp.MAX)
+
+    def sum(self, x):
+        return self._reduce(x, None if self.dist is None else self.dist.ReduceOp.SUM)
+
+    def gather(self, values):
+        """Every rank's list, concatenated in rank order (on every rank)."""
+        from paper_1206_0919_gb300 import serving
+        return serving.gather(values, self.dist)
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
+def job_rate(world, units_per_rank, seconds):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (weak scaling: each rank processes the same count)."""
+    return world * units_per_rank / seconds
+
+
 # ---------------------------------------------------------- CPU oracle ----
 
 def oracle_rate(N, max_steps=3, target_s=10.0, threads=None):
@@ -245,11 +312,15 @@ def run_reference(args):
     value = side ** 3 * args.steps / dt
     sample = (f"{args.steps} full oracle steps of the centred {side}^3 crop of the {N}^3 state "
               f"({dt:.1f} s)")
+    cfg = workload_config(args)
+    cfg["precision"] = "fp64"  # the oracle computes in FP64 whatever --precision says
+    cfg["bench_step"] = (f"one full split step of the oracle on the centred {side}^3 crop "
+                         f"(a bounded sample of the {N}^3 event)")
     out = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": workload_config(args),
+        "data": "synthetic", "config": cfg,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -271,60 +342,73 @@ def run_ours(args):
     if not torch.cuda.is_available():
         raise RuntimeError("bench.py needs a CUDA device (no CPU fallback exists)")
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
+    ranks = Ranks("nccl", torch.device("cuda", local))
 
     N = args.grid
     ncell = N ** 3
-    prims = workload_prims(N, seed=2 + 1000 * rank)
+    prims = workload_prims(N, seed=workload_seed(rank))
     stream = torch.cuda.Stream()
     solver = S.Solver((N, N, N), precision=args.precision, stream=stream.cuda_stream,
                       device=local)
+    # the event's initial conserved state, resident on the device in FP64
     solver.set_primitives(*prims.as_list())
-    solver.step(args.warmup)
+    U0 = [torch.empty((N, N, N), dtype=torch.float64, device="cuda") for _ in range(5)]
+    solver.get_conserved(U0)
+
+    def event(marks=None):
+        """One benchmark step: the event from its initial state (set through
+        the C ABI from the device arrays, input check included), then its
+        200 full split steps (six-step CUDA graphs)."""
+        solver.set_conserved(U0)
+        if marks:
+            marks[0].record(stream)
+        solver.step(EVENT_STEPS)
+        if marks:
+            marks[1].record(stream)
+
+    for _ in range(args.warmup):
+        event()
     solver.sync()
 
-    # timed region: K steps, events between steps on the solver's stream
+    # timed region: K events; CUDA events around each event's steps give the
+    # sweep kernels' own time inside it
+    marks = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+             for _ in range(args.steps)]
     sampler = ClockSampler(local)
     sampler.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
+    ranks.barrier()
     torch.cuda.synchronize()
     t_wall0 = time.time()
     torch.cuda.nvtx.range_push("timed_steps")  # profilers can filter on this range
     ev0.record(stream)
-    solver.step(args.steps)  # K steps enqueued at once (six-step CUDA graphs)
+    for k in range(args.steps):
+        event(marks[k])
     ev1.record(stream)
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
-    barrier()
+    ranks.barrier()
     t_wall1 = time.time()
     sampler.stop()
     clocks = sampler.summary(t_wall0, t_wall1)
-    ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * ncell * args.steps / (ms / 1e3)
+    ms = ranks.max(ev0.elapsed_time(ev1))
+    sweep_ms = ranks.max(sum(a.elapsed_time(b) for a, b in marks))
+    units = ncell * EVENT_STEPS * args.steps  # cell-updates of one rank
+    value = job_rate(world, units, ms / 1e3)
 
-    # roofline of the sweep kernel (the only kernel of a step: 3 launches)
+    # roofline of the sweep kernel (three launches per split step)
     word = 8 if args.precision == "fp64" else 4
     bytes_per_launch = ncell * 5 * word * 2  # read + write of the five conserved fields
-    launch_s = (ms / 1e3) / (3 * args.steps)
+    launch_s = (sweep_ms / 1e3) / (3 * EVENT_STEPS * args.steps)
     achieved = bytes_per_launch / launch_s / 1e9
     peak, peak_kind = measured_peak()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind,
                 "traffic": committed_traffic(args.precision, N),
                 "kernel": f"sweep_kernel ({args.precision})",
-                "algorithmic_bytes_per_launch": bytes_per_launch}
+                "algorithmic_bytes_per_launch": bytes_per_launch,
+                "launch_us": launch_s * 1e6,
+                "timed": "CUDA events around the 200 split steps of every timed event"}
 
     tuning = {"xyz"[a]: {"variant": v, "range_len": r} for a, (v, r) in enumerate(solver.tuning())}
 
@@ -348,21 +432,19 @@ def run_ours(args):
     solver.set_primitives(*host_in)
     solver.step(2)
     solver.get_primitives(host_out)
-    barrier()
+    ranks.barrier()
     t0 = time.perf_counter()
     for _ in range(args.e2e_events):
         solver.set_primitives(*host_in)
         solver.step(EVENT_STEPS)
         solver.get_primitives(host_out)
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * ncell * EVENT_STEPS * args.e2e_events / e2e_s, "unit": UNIT,
+    e2e_s = ranks.max(time.perf_counter() - t0)
+    e2e = {"value": job_rate(world, ncell * EVENT_STEPS * args.e2e_events, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": 5 * 8 * ncell, "d2h_bytes_per_step": 6 * 8 * ncell,
            "step": f"one event: set_primitives from pinned host, {EVENT_STEPS} steps, "
                    "get_primitives to pinned host"}
+    solver.close()
+    del U0
 
     extra = {}
     if not args.no_fp64_path and args.precision != "fp64":
@@ -380,7 +462,12 @@ def run_ours(args):
             r64 = ncell * k64 / (e0.elapsed_time(e1) / 1e3)
         extra["fp64_path"] = {"value": r64, "unit": UNIT,
                               "speedup_of_value": value / world / r64}
-    solver.close()
+    if not args.no_legs:
+        extra["precisions"] = precision_legs(args, stream, local, prims, value / world)
+        extra["alu_peaks"] = alu_peaks(local, stream)
+        extra["batch64"] = batch_leg(ranks, stream, local, n_events=64, precision="mixed",
+                                     steps=100, warmup=12)
+        extra["serve"] = serve_legs(args, ranks, local, rates=(60.0, 200.0), n_events=150)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -389,22 +476,67 @@ def run_ours(args):
                "sample": f"{steps} full oracle step(s) of the {N}^3 state ({t:.1f} s)"}
 
     if rank == 0:
+        cfg = workload_config(args)
+        cfg["bench_step"] = (f"one event: initial state set from device-resident FP64 arrays "
+                             f"through shasta_set_conserved (input check included), then "
+                             f"{EVENT_STEPS} full split steps")
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "mixed": "f32+f64", "fp64": "f64"}[args.precision],
-            "data": "synthetic", "config": workload_config(args),
+            "data": "synthetic", "config": cfg,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": 3 * args.steps, "clocks": clocks,
+            # per event: 600 sweeps, the input check and five conversions
+            "gpu_launches": (3 * EVENT_STEPS + 6) * args.steps, "clocks": clocks,
             "tuning": tuning,
             "per_axis_sweep": per_axis,
         }
         out.update(extra)
         print(json.dumps(out), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    ranks.close()
     return 0
+
+
+def precision_legs(args, stream, local, prims, fp32_rate, k=30):
+    """The same workload with the recovery in double-float (MIXED) and in
+    double (MIXED_FP64): cell-updates/s over k split steps after the
+    autotuner, and the slowdown against the headline FP32 rate."""
+    from paper_1206_0919_gb300 import shasta as S
+
+    N = args.grid
+    out = {}
+    for prec in ("mixed", "mixed_fp64"):
+        with S.Solver((N, N, N), precision=prec, stream=stream.cuda_stream, device=local) as s:
+            s.set_primitives(*prims.as_list())
+            s.step(6)  # includes the autotuner
+            secs = timed_steps(s, stream, k)
+        rate = N ** 3 * k / secs
+        out[prec] = {"value": rate, "unit": UNIT, "steps": k, "ms_per_step": secs * 1e3 / k,
+                     "time_vs_fp32": fp32_rate / rate}
+    out["recovery"] = {"mixed": "D = E^2 - |M|^2 in double-float on the FP32 pipe",
+                       "mixed_fp64": "D, root, p and w in IEEE double from the float state"}
+    return out
+
+
+def alu_peaks(local, stream):
+    """Measured FP32 and FP64 CUDA-core rates of this GPU (the arithmetic
+    roofs beside the HBM one), with the clocks seen while they ran."""
+    from paper_1206_0919_gb300 import shasta as S
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    t0 = time.time()
+    out = {}
+    for kind in ("fp32", "fp64"):
+        flops, secs = S.alu_peak(kind, device=local, stream=stream.cuda_stream)
+        out[kind] = {"tflops": flops / 1e12, "launch_ms": secs * 1e3}
+    t1 = time.time()
+    sampler.stop()
+    out["clocks"] = sampler.summary(t0, t1)
+    out["how"] = ("independent chains of dependent fused multiply-adds on every SM "
+                  "(shasta_alu_peak; one FMA = 2 flops), three launches of >= 20 ms, CUDA events")
+    return out
 
 
 def run_kernels_only(args):
@@ -448,6 +580,70 @@ def batch_config(args, precision):
     }
 
 
+def _batch_timed(ranks, stream, local, evs, host, precision, steps, warmup):
+    """Adds the events to one batch, runs `warmup` steps (the autotuner
+    times its choices there) and times `steps` steps of the whole batch."""
+    import torch
+
+    from paper_1206_0919_gb300 import shasta as S
+
+    total = sum(ev["N"] ** 3 for ev in evs)
+    b = S.Batch(total + 64 * len(evs), precision=precision, max_events=len(evs),
+                stream=stream.cuda_stream, device=local)
+    ids = [b.add_primitives((ev["N"],) * 3, h) for ev, h in zip(evs, host)]
+    b.step(warmup)
+    b.sync()
+    info = b.info()
+    launches0 = info["launches"]
+    sampler = ClockSampler(local)
+    sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ranks.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    torch.cuda.nvtx.range_push("timed_steps")  # profilers can filter on this range
+    ev0.record(stream)
+    b.step(steps)
+    ev1.record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    ranks.barrier()
+    t_wall1 = time.time()
+    sampler.stop()
+    ms = ranks.max(ev0.elapsed_time(ev1))
+    launches = b.info()["launches"] - launches0
+    bytes_per_step = total * 5 * 4 * 2 * 3
+    achieved = bytes_per_step / (ms / 1e3 / steps) / 1e9
+    peak, peak_kind = measured_peak()
+    leg = {
+        "value": job_rate(ranks.world, total * steps, ms / 1e3), "unit": UNIT,
+        "steps": steps, "warmup": warmup, "ms_per_step": ms / steps,
+        "precision": precision, "events": len(evs), "cells": total,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                     "kernel": f"sweep_batch_kernel ({precision}), all launches of a step",
+                     "algorithmic_bytes_per_step": bytes_per_step},
+        "launches_per_step": info["launches_per_step"], "items_per_step": info["items_per_step"],
+        "gpu_launches": launches, "clocks": sampler.summary(t_wall0, t_wall1),
+    }
+    return leg, b, ids
+
+
+def batch_leg(ranks, stream, local, n_events=64, precision="mixed", steps=100, warmup=12):
+    """Config 3 on the headline line: 64 uneven events (hot spots + radial
+    flow, N from {48, 64, 96, 128, 160}) advanced as one batch, one launch
+    per (sweep slot, axis) over the work list of all events."""
+    from paper_1206_0919_gb300 import workloads as W
+
+    evs = W.batch_events(n_events=n_events, seed=3 + 1000 * ranks.rank)
+    host = [W.event_prims(ev).as_list() for ev in evs]
+    leg, b, _ = _batch_timed(ranks, stream, local, evs, host, precision, steps, warmup)
+    b.close()
+    leg["workload"] = f"batch_{n_events}_events"
+    leg["sizes"] = "N uniform in {48,64,96,128,160}, grids N^3, 5-40 hot spots, v_r = 0.1 r/R_box"
+    return leg
+
+
 def run_batch(args):
     """64 uneven events (hot spots + radial flow) advanced as one batch: one
     launch per (sweep slot, axis) over the work list of all events."""
@@ -461,60 +657,16 @@ def run_batch(args):
     if not torch.cuda.is_available():
         raise RuntimeError("bench.py needs a CUDA device (no CPU fallback exists)")
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    ranks = Ranks("nccl", torch.device("cuda", local))
     precision = args.precision if args.precision != "fp64" else "mixed"
     args.events = args.events or 64
     evs = W.batch_events(n_events=args.events, seed=3 + 1000 * rank)
-    cells = [ev["N"] ** 3 for ev in evs]
-    total = sum(cells)
+    total = sum(ev["N"] ** 3 for ev in evs)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
     host = [[pin(a) for a in W.event_prims(ev).as_list()] for ev in evs]
     stream = torch.cuda.Stream()
-    cap = total + 64 * len(evs)
-    b = S.Batch(cap, precision=precision, max_events=len(evs), stream=stream.cuda_stream,
-                device=local)
-    ids = [b.add_primitives((ev["N"],) * 3, h) for ev, h in zip(evs, host)]
-    b.step(args.warmup)  # includes the autotuner's timing
-    b.sync()
-    info = b.info()
-    launches0 = info["launches"]
-
-    sampler = ClockSampler(local)
-    sampler.start()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
-    t_wall0 = time.time()
-    torch.cuda.nvtx.range_push("timed_steps")  # profilers can filter on this range
-    ev0.record(stream)
-    b.step(args.steps)
-    ev1.record(stream)
-    torch.cuda.nvtx.range_pop()
-    torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
-    t_wall1 = time.time()
-    sampler.stop()
-    clocks = sampler.summary(t_wall0, t_wall1)
-    ms = ev0.elapsed_time(ev1)
-    launches = b.info()["launches"] - launches0
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * total * args.steps / (ms / 1e3)
-    launches_per_step = info["launches_per_step"]
-    bytes_per_step = total * 5 * 4 * 2 * 3
-    achieved = bytes_per_step / (ms / 1e3 / args.steps) / 1e9
-    peak, peak_kind = measured_peak()
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
-                "kernel": f"sweep_batch_kernel ({precision}), all launches of a step",
-                "algorithmic_bytes_per_step": bytes_per_step}
+    leg, b, ids = _batch_timed(ranks, stream, local, evs, host, precision, args.steps,
+                               args.warmup)
 
     # end to end through the public API: every event added from pinned host
     # arrays, 100 steps, primitives of every event read back to pinned host
@@ -527,8 +679,8 @@ def run_batch(args):
     b.step(100)
     for i, o in zip(ids, outs):
         b.get_primitives(i, o)
-    e2e_s = time.perf_counter() - t0
-    e2e = {"value": world * total * 100 / e2e_s, "unit": UNIT,
+    e2e_s = ranks.max(time.perf_counter() - t0)
+    e2e = {"value": job_rate(world, total * 100, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": 5 * 8 * total, "d2h_bytes_per_step": 6 * 8 * total,
            "step": "all events: add from pinned host (includes the autotuner), 100 steps, "
                    "primitives to pinned host"}
@@ -553,21 +705,20 @@ def run_batch(args):
 
     if rank == 0:
         out = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
+            "metric": METRIC, "value": leg["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": leg["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "mixed": "f32+f64"}[precision],
             "data": "synthetic", "config": batch_config(args, precision),
-            "roofline": roofline, "cpu_baseline": None, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clocks,
-            "batch": {"cells": total, "launches_per_step": launches_per_step,
-                      "items_per_step": info["items_per_step"]},
+            "roofline": leg["roofline"], "cpu_baseline": None, "e2e": e2e,
+            "gpu_launches": leg["gpu_launches"], "clocks": leg["clocks"],
+            "batch": {"cells": total, "launches_per_step": leg["launches_per_step"],
+                      "items_per_step": leg["items_per_step"]},
             "one_context_per_event": {"value": single_rate, "unit": UNIT,
-                                      "batch_speedup": value / world / single_rate},
+                                      "batch_speedup": leg["value"] / world / single_rate},
         }
         print(json.dumps(out), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    ranks.close()
     return 0
 
 
@@ -588,98 +739,126 @@ def serve_config(args):
     }
 
 
-def run_serve(args):
-    """Poisson arrivals replayed in real time against the serving loop; each
-    rank runs its own server on its GPU with every world-th event."""
+def serve_inputs():
+    """Two seeded hot-spot states per (N, EoS) of the serving mix, reused
+    along the stream (generating a fresh 192^3 state per event would take
+    minutes)."""
     import numpy as np
-    import torch
 
-    from paper_1206_0919_gb300 import serving
-    from paper_1206_0919_gb300 import shasta as S
     from paper_1206_0919_gb300 import workloads as W
 
-    rank, world, local = dist_env()
-    if not torch.cuda.is_available():
-        raise RuntimeError("bench.py needs a CUDA device (no CPU fallback exists)")
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    precision = args.precision if args.precision != "fp64" else "fp32"
-    args.events = args.events or 300
-    stream = serving.shard(
-        W.serving_stream(n_events=args.events * world, rate_hz=args.rate * world, seed=4),
-        rank, world)
     pool = {}
     for N in W.SERVE_SIZES:
         for eos in ("ideal", "bag"):
             for v in range(2):
                 pr = W.hot_spots(N=N, seed=500 + 10 * N + 2 * v + (eos == "bag"), n_spots=20)
                 pool[(N, eos, v)] = [np.ascontiguousarray(a) for a in pr.as_list()]
-    inputs = lambda ev: pool[(ev["N"], ev["eos"], ev["seed"] % 2)]
-    budget = int(args.budget_gb * (1 << 30))
+    return lambda ev: pool[(ev["N"], ev["eos"], ev["seed"] % 2)]
+
+
+def serve_stream_leg(ranks, local, inputs, rate, n_events, precision, budget_gb=48.0,
+                     max_resident=64, steps_per_round=6, warmup=3):
+    """One Poisson stream (every world-th event per rank, `rate` arrivals
+    per second per rank) replayed in real time against a fresh server."""
+    import numpy as np
+
+    from paper_1206_0919_gb300 import serving
+    from paper_1206_0919_gb300 import shasta as S
+    from paper_1206_0919_gb300 import workloads as W
+
+    stream = serving.shard(
+        W.serving_stream(n_events=n_events * ranks.world, rate_hz=rate * ranks.world, seed=4),
+        ranks.rank, ranks.world)
+    budget = int(budget_gb * (1 << 30))
     srv = S.Server(budget, precision=precision, staging_bytes=budget // 6,
-                   max_resident=args.max_resident, steps_per_round=args.steps_per_round,
-                   device=local)
+                   max_resident=max_resident, steps_per_round=steps_per_round, device=local)
     # warm-up: a few small events through the whole loop
     warm = [dict(t_arrival=0.0, N=64, eos=("ideal", "bag")[i % 2], steps=6, seed=i)
-            for i in range(max(1, args.warmup))]
+            for i in range(max(1, warmup))]
     serving.replay(srv, warm, inputs)
     st0 = srv.stats()
-
     sampler = ClockSampler(local)
     sampler.start()
-    if dist is not None:
-        dist.barrier()
+    ranks.barrier()
     t_wall0 = time.time()
     recs = serving.replay(srv, stream, inputs)
     t_wall1 = time.time()
     sampler.stop()
-    clocks = sampler.summary(t_wall0, t_wall1)
     st1 = srv.stats()
     srv.close()
-    span = max(r["t_done"] for r in recs) - min(r["t_arrival"] for r in recs)
-    lat_arr = [r["t_done"] - r["t_arrival"] for r in recs]
-    lat_sub = [r["t_done"] - r["t_submit"] for r in recs]
-    cells = sum(r["N"] ** 3 * r["steps"] for r in recs)
-    refusals = sum(r["refusals"] for r in recs)
-    if dist is not None:
-        t = torch.tensor([span], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        span = float(t.item())
-    lat_arr = serving.gather(lat_arr, dist)
-    lat_sub = serving.gather(lat_sub, dist)
-    n_all = len(lat_arr)
-    cells_all = serving.gather([cells], dist)
-    value = n_all / span
+    span = ranks.max(max(r["t_done"] for r in recs) - min(r["t_arrival"] for r in recs))
+    lat_arr = ranks.gather([r["t_done"] - r["t_arrival"] for r in recs])
+    lat_sub = ranks.gather([r["t_done"] - r["t_submit"] for r in recs])
+    cells = sum(ranks.gather([sum(r["N"] ** 3 * r["steps"] for r in recs)]))
+    a, b = serving.summary(lat_arr), serving.summary(lat_sub)
+    return {
+        "value": len(lat_arr) / span, "unit": "events/s", "events": len(lat_arr),
+        "offered_events_per_s": rate * ranks.world, "span_s": span,
+        "latency_s": {"p50": a["p50"], "p99": a["p99"], "mean": a["mean"], "max": a["max"],
+                      "from": "scheduled arrival to results in the caller's buffers"},
+        "latency_from_submit_s": {"p50": b["p50"], "p99": b["p99"]},
+        "served_cell_updates_per_s": cells / span,
+        "queue_full_refusals": sum(ranks.gather([sum(r["refusals"] for r in recs)])),
+        "peak_resident": st1["peak_resident"],
+        "worker_time_s": {k[2:]: round(st1[k] - st0[k], 4) for k in st1 if k.startswith("t_")},
+        "e2e_bytes_per_event": {"h2d": int(np.mean([40 * r["N"] ** 3 for r in recs])),
+                                "d2h": int(np.mean([48 * r["N"] ** 3 for r in recs]))},
+        "gpu_launches": int(st1["sweep_launches"] - st0["sweep_launches"]),
+        "clocks": sampler.summary(t_wall0, t_wall1),
+    }
+
+
+def serve_legs(args, ranks, local, rates=(60.0, 200.0), n_events=150):
+    """Config 4 on the headline line: short Poisson streams at each rate."""
+    inputs = serve_inputs()
+    precision = args.precision if args.precision not in ("fp64",) else "fp32"
+    out = {"workload": "serve_poisson",
+           "sizes": "N in {64,96,128,192} with probabilities 0.4/0.3/0.2/0.1, grids N^3",
+           "eos": "alternating: ideal p=e/3 / bag (B=0.1, e_c=0.5)", "steps_per_event": 150,
+           "precision": precision, "events_per_stream": n_events * ranks.world}
+    for rate in rates:
+        out[f"{rate:g}_per_s"] = serve_stream_leg(ranks, local, inputs, rate, n_events, precision)
+    return out
+
+
+def run_serve(args):
+    """Poisson arrivals replayed in real time against the serving loop; each
+    rank runs its own server on its GPU with every world-th event."""
+    import torch
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device (no CPU fallback exists)")
+    torch.cuda.set_device(local)
+    ranks = Ranks("nccl", torch.device("cuda", local))
+    precision = args.precision if args.precision != "fp64" else "fp32"
+    args.events = args.events or 300
+    leg = serve_stream_leg(ranks, local, serve_inputs(), args.rate, args.events, precision,
+                           budget_gb=args.budget_gb, max_resident=args.max_resident,
+                           steps_per_round=args.steps_per_round, warmup=args.warmup)
     if rank == 0:
-        a, b = serving.summary(lat_arr), serving.summary(lat_sub)
         out = {
-            "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
-            "steps": len(recs), "warmup": len(warm), "ms_per_step": span * 1e3 / max(1, len(recs)),
+            "metric": METRIC, "value": leg["value"], "unit": "events/s", "n_gpus": world,
+            "steps": leg["events"], "warmup": max(1, args.warmup),
+            "ms_per_step": leg["span_s"] * 1e3 / max(1, leg["events"]),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "mixed": "f32+f64"}[precision], "data": "synthetic",
             "config": serve_config(args),
-            "latency_s": {"p50": a["p50"], "p99": a["p99"], "mean": a["mean"], "max": a["max"],
-                          "from": "scheduled arrival to results in the caller's buffers"},
-            "latency_from_submit_s": {"p50": b["p50"], "p99": b["p99"]},
-            "served_cell_updates_per_s": sum(cells_all) / span,
-            "offered_events_per_s": args.rate * world,
-            "queue_full_refusals": refusals,
-            "peak_resident": st1["peak_resident"],
-            "worker_time_s": {k[2:]: round(st1[k] - st0[k], 4) for k in st1 if k.startswith("t_")},
-            "e2e": {"value": value, "unit": "events/s",
-                    "h2d_bytes_per_step": int(np.mean([40 * r["N"] ** 3 for r in recs])),
-                    "d2h_bytes_per_step": int(np.mean([48 * r["N"] ** 3 for r in recs])),
+            "latency_s": leg["latency_s"], "latency_from_submit_s": leg["latency_from_submit_s"],
+            "served_cell_updates_per_s": leg["served_cell_updates_per_s"],
+            "offered_events_per_s": leg["offered_events_per_s"],
+            "queue_full_refusals": leg["queue_full_refusals"],
+            "peak_resident": leg["peak_resident"], "worker_time_s": leg["worker_time_s"],
+            "e2e": {"value": leg["value"], "unit": "events/s",
+                    "h2d_bytes_per_step": leg["e2e_bytes_per_event"]["h2d"],
+                    "d2h_bytes_per_step": leg["e2e_bytes_per_event"]["d2h"],
                     "step": "one event (mean bytes): host arrays in, 150 steps, primitives "
                             "to host buffers"},
-            "gpu_launches": int(st1["sweep_launches"] - st0["sweep_launches"]),
-            "clocks": clocks, "roofline": None, "cpu_baseline": None,
+            "gpu_launches": leg["gpu_launches"], "clocks": leg["clocks"], "roofline": None,
+            "cpu_baseline": None,
         }
         print(json.dumps(out), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    ranks.close()
     return 0
 
 

@@ -60,11 +60,20 @@ enum { SHASTA_BC_REFLECT = 0, SHASTA_BC_PERIODIC = 1, SHASTA_BC_FROZEN = 2 };
  * by the fixed-point iteration of Sec. 3; single contexts, FP64 and FP32. */
 enum { SHASTA_EOS_IDEAL = 0, SHASTA_EOS_BAG = 1, SHASTA_EOS_TABLE = 2 };
 
-/* Precision of the device state and arithmetic.  FP64: everything in double.
- * FP32: state, transport, limiter and recovery in float.  MIXED: state,
- * transport and limiter in float; the recovery of the primitives (where
- * 1 - v^2 cancels as v -> 1, Sec. 4-5) in double. */
-enum { SHASTA_FP64 = 0, SHASTA_FP32 = 1, SHASTA_MIXED = 2 };
+/* Precision of the device state and arithmetic (Sec. 4-5: single precision
+ * throughout, or double precision for the parts that lose accuracy as
+ * v -> 1, where 1 - v^2 cancels).  FP64: everything in double.  FP32:
+ * state, transport, limiter and recovery in float.  MIXED: state,
+ * transport, limiter and most of the recovery in float; only the cancelling
+ * difference D = E^2 - |M|^2 of the recovery is formed at about double
+ * accuracy, as a compensated double-float evaluation on the FP32 pipe
+ * (error-free products and sums).  MIXED_FP64: state, transport and
+ * limiter in float; the whole recovery at every sweep position (D, the
+ * closed-form root, p and the velocity along the sweep) in IEEE double from
+ * the float state, rounded to float for the transport; single contexts
+ * with the ideal or bag EoS.  The primitive output (shasta_get_primitives)
+ * and the totals are computed in double for every precision. */
+enum { SHASTA_FP64 = 0, SHASTA_FP32 = 1, SHASTA_MIXED = 2, SHASTA_MIXED_FP64 = 3 };
 
 enum { SHASTA_MEM_HOST = 0, SHASTA_MEM_DEVICE = 1 };
 
@@ -91,10 +100,10 @@ typedef struct shasta_eos {
 } shasta_eos;
 
 typedef struct shasta_opts {
-  int precision; /* SHASTA_FP64 / SHASTA_FP32 / SHASTA_MIXED */
+  int precision; /* SHASTA_FP64 / SHASTA_FP32 / SHASTA_MIXED / SHASTA_MIXED_FP64 */
   double eta;    /* outer antidiffusion coefficient; Sec. 3 uses 1/8 */
   double delta;  /* recovery clamps |M| to (1 - delta) E; 0 selects 1e-10 (FP64)
-                    or 1e-6 (FP32, MIXED) */
+                    or 1e-6 (FP32, MIXED, MIXED_FP64) */
   void* stream;  /* cudaStream_t to enqueue on; NULL: the context makes its own */
   int device;    /* CUDA device ordinal */
   int check_input; /* nonzero: set calls scan the state and return
@@ -221,16 +230,19 @@ shasta_status shasta_totals(shasta_ctx* ctx, double out[5]);
  * the call returns without waiting; out is ready when the stream reaches it.
  * The caller keeps ownership of every pointer.
  *
- * The first call on a device looks up the address of the fixed array on
- * that device (it may load the library's device code there); make that
- * first call before any stream capture on the device.  All calls on a device
+ * Every call looks up the address of the fixed array on the current device
+ * (a runtime table search, no allocation; looking it up each time keeps it
+ * right after a device reset, which may reload the library's device code at
+ * another address).  The first call on a device may load the library's
+ * device code there; make that first call before any stream capture on the
+ * device.  All calls on a device
  * share the array, which keeps the last call's partials: each call writes
  * every partial it reads, so nothing needs clearing, but calls whose work
  * overlaps on the GPU (two streams, or two threads) race on the array and
  * must be ordered by the caller.
  *
  * Errors: EINVAL (out NULL, a field NULL with n > 0, n larger than
- * SHASTA_TOTALS_NOALLOC_MAX_CELLS, or a device ordinal of 64 or more),
+ * SHASTA_TOTALS_NOALLOC_MAX_CELLS),
  * ECUDA (no current device, the address lookup or a launch failed).  No
  * message is kept: the status is the whole report. */
 #define SHASTA_TOTALS_NOALLOC_MAX_CELLS 67108864ull /* 2^26 cells, e.g. 406^3 */
@@ -238,6 +250,25 @@ shasta_status shasta_totals(shasta_ctx* ctx, double out[5]);
 shasta_status shasta_totals_noalloc(const double* E, const double* Mx, const double* My,
                                     const double* Mz, const double* R, size_t n, double* out,
                                     void* stream);
+
+/* Measured CUDA-core throughput of a device (the paper has no counterpart:
+ * this is the arithmetic roof that the benchmark reports beside the HBM
+ * roof, since the sweeps are bound by instruction issue).
+ *
+ * kind: SHASTA_ALU_FP32 or SHASTA_ALU_FP64.  Runs independent chains of
+ * dependent fused multiply-adds on every SM of `device` on `stream` (a
+ * cudaStream_t of that device, NULL for the legacy default stream), growing
+ * the chain length until one launch takes at least 20 ms, and times three
+ * launches with CUDA events.  Writes the rate in floating-point operations
+ * per second (one fused multiply-add = 2) to *flops_per_s and, when
+ * seconds_per_launch is not NULL, the time of one launch.  Synchronous.
+ * Allocates and frees a small output buffer; changes no device setting.
+ * Errors: EINVAL (bad kind, flops_per_s NULL), ENOMEM, ECUDA. */
+#define SHASTA_ALU_FP32 0
+#define SHASTA_ALU_FP64 1
+shasta_status shasta_alu_peak(int kind, int device, void* stream, double* flops_per_s,
+                              double* seconds_per_launch);
+
 
 /* Number of full steps taken since the state was last set (the permutation
  * phase is this mod 6). */

@@ -39,8 +39,10 @@ UNITS = [
     ("sweep_f32_noaf.cu", FAST),
     ("sweep_split.cu", FAST),
     ("sweep_mixed.cu", FAST),
+    ("sweep_mixed64.cu", FAST),
     ("batch_f32.cu", FAST),
     ("batch_mixed.cu", FAST),
+    ("alu_peak.cu", FAST),
 ]
 
 

@@ -22,10 +22,10 @@ LIB_PATH = os.path.join(HERE, "libshasta.so")
 OK, EINVAL, ENOMEM, EAGAIN, EUNPHYSICAL, ETIMEOUT, ECUDA, ENOTFOUND = range(8)
 BC_REFLECT, BC_PERIODIC, BC_FROZEN = 0, 1, 2
 EOS_IDEAL, EOS_BAG, EOS_TABLE = 0, 1, 2
-FP64, FP32, MIXED = 0, 1, 2
+FP64, FP32, MIXED, MIXED_FP64 = 0, 1, 2, 3
 MEM_HOST, MEM_DEVICE = 0, 1
 
-PRECISIONS = {"fp64": FP64, "fp32": FP32, "mixed": MIXED}
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "mixed": MIXED, "mixed_fp64": MIXED_FP64}
 BCS = {"reflect": BC_REFLECT, "periodic": BC_PERIODIC, "frozen": BC_FROZEN}
 
 
@@ -103,6 +103,8 @@ SIGNATURES = {
     "shasta_get_primitives": (C.c_int, [_vp] + [_vp] * 6 + [C.c_int]),
     "shasta_totals": (C.c_int, [_vp, _dp]),
     "shasta_totals_noalloc": (C.c_int, [_vp] * 5 + [C.c_size_t, _vp, _vp]),
+    "shasta_alu_peak": (C.c_int, [C.c_int, C.c_int, _vp, C.POINTER(C.c_double),
+                                  C.POINTER(C.c_double)]),
     "shasta_steps_done": (C.c_int64, [_vp]),
     "shasta_set_step_counter": (C.c_int, [_vp, C.c_int64]),
     "shasta_counters": (C.c_int, [_vp, C.POINTER(C.c_int64)]),
@@ -240,6 +242,15 @@ def totals_noalloc(E, Mx, My, Mz, R, out, stream=None):
         raise ShastaError(st, "shasta_totals_noalloc failed"
                           + (" (more cells than its fixed scratch holds, or a NULL pointer)"
                              if st == EINVAL else ""))
+
+
+def alu_peak(kind="fp32", device=0, stream=None):
+    """Measured CUDA-core rate of `device` (shasta_alu_peak): (floating-point
+    operations per second, seconds per timed launch); kind "fp32" or "fp64"."""
+    flops, secs = C.c_double(), C.c_double()
+    _check(lib().shasta_alu_peak({"fp32": 0, "fp64": 1}[kind], device, stream, C.byref(flops),
+                                 C.byref(secs)))
+    return flops.value, secs.value
 
 
 class Solver:
