@@ -270,6 +270,8 @@ void launch_choice(const shasta_ctx* c, int axis, int& variant, long long& range
 cudaError_t launch_params(shasta_ctx* c, int axis, const SweepParams& P) {
   if (c->o.precision == SHASTA_FP64) return launch_sweep_f64(P, axis, c->eos.kind, c->stream);
   if (c->o.precision == SHASTA_MIXED) return launch_sweep_mixed(P, axis, c->eos.kind, c->stream);
+  if (c->o.precision == SHASTA_MIXED_FP64)
+    return launch_sweep_mixed64(P, axis, c->eos.kind, c->stream);
   if (c->o.scheme == SHASTA_SCHEME_NO_ANTIFLUX)
     return launch_sweep_f32_noaf(P, axis, c->eos.kind, c->stream);
   if (c->o.scheme == SHASTA_SCHEME_SPLIT)
@@ -412,10 +414,11 @@ shasta_status shasta_create(const shasta_grid* g, double dx, double lambda, cons
     opts = *o;
   else
     shasta_default_opts(&opts);
-  if (opts.precision < SHASTA_FP64 || opts.precision > SHASTA_MIXED)
+  if (opts.precision < SHASTA_FP64 || opts.precision > SHASTA_MIXED_FP64)
     return fail(nullptr, SHASTA_EINVAL, "unknown precision");
   if (opts.precision != SHASTA_FP64 && (long long)g->nx * g->ny * g->nz >= (1LL << 32))
     return fail(nullptr, SHASTA_EINVAL, "FP32 / MIXED grids hold fewer than 2^32 cells");
+  const bool mixed = opts.precision == SHASTA_MIXED || opts.precision == SHASTA_MIXED_FP64;
   if (!(opts.eta >= 0.0 && opts.eta <= 0.5)) return fail(nullptr, SHASTA_EINVAL, "need 0 <= eta <= 0.5");
   if (!(opts.delta >= 0.0 && opts.delta < 0.5)) return fail(nullptr, SHASTA_EINVAL, "need 0 <= delta < 0.5");
   if (opts.scheme != SHASTA_SCHEME_FUSED && opts.scheme != SHASTA_SCHEME_NO_ANTIFLUX &&
@@ -437,8 +440,7 @@ shasta_status shasta_create(const shasta_grid* g, double dx, double lambda, cons
   if (e.kind == SHASTA_EOS_BAG && !(e.B >= 0.0 && 4.0 * e.B <= e.e_c))
     return fail(nullptr, SHASTA_EINVAL, "bag EoS needs 0 <= 4B <= e_c");
   if (e.kind == SHASTA_EOS_TABLE) {
-    if (opts.precision == SHASTA_MIXED)
-      return fail(nullptr, SHASTA_EINVAL, "a tabulated EoS runs in FP64 or FP32");
+    if (mixed) return fail(nullptr, SHASTA_EINVAL, "a tabulated EoS runs in FP64 or FP32");
     if (opts.scheme == SHASTA_SCHEME_NO_ANTIFLUX && opts.precision == SHASTA_FP32)
       return fail(nullptr, SHASTA_EINVAL, "no FP32 transport-only kernels for a tabulated EoS");
     if (!e.table || e.table_n < 2 || e.table_n > (1 << 26) || !(e.table_de > 0.0) ||
@@ -556,10 +558,13 @@ shasta_status shasta_create(const shasta_grid* g, double dx, double lambda, cons
   if (err != cudaSuccess) return bail(err, "cudaMallocHost");
   if (opts.precision != SHASTA_FP64) {
     err = opts.precision == SHASTA_MIXED                 ? prepare_sweep_mixed(c->occ)
+          : opts.precision == SHASTA_MIXED_FP64          ? prepare_sweep_mixed64(c->occ)
           : opts.scheme == SHASTA_SCHEME_NO_ANTIFLUX ? prepare_sweep_f32_noaf(c->occ)
                                                      : prepare_sweep_f32(c->occ);
     if (err != cudaSuccess) return bail(err, "prepare sweep kernels");
-    c->wpb = opts.precision == SHASTA_MIXED ? sweep_warps_per_block_mixed() : sweep_warps_per_block_f32();
+    c->wpb = opts.precision == SHASTA_MIXED        ? sweep_warps_per_block_mixed()
+             : opts.precision == SHASTA_MIXED_FP64 ? sweep_warps_per_block_mixed64()
+                                                   : sweep_warps_per_block_f32();
   }
   if (opts.stream) {
     c->stream = (cudaStream_t)opts.stream;

@@ -5,12 +5,12 @@
 namespace shasta {
 
 cudaError_t prepare_batch_f32(int occupancy[3][3][2]) {
-  return launch::prepare<false, launch::BATCH>(occupancy);
+  return launch::prepare<fast::REC_F32, launch::BATCH>(occupancy);
 }
 
 cudaError_t launch_batch_f32(const SweepParams& P, const BatchList& L, int axis, int eos,
                              cudaStream_t s) {
-  return launch::launch_batch<false>(P, L, axis, eos, s);
+  return launch::launch_batch<fast::REC_F32>(P, L, axis, eos, s);
 }
 
 }  // namespace shasta

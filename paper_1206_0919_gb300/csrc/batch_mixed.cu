@@ -5,12 +5,12 @@
 namespace shasta {
 
 cudaError_t prepare_batch_mixed(int occupancy[3][3][2]) {
-  return launch::prepare<true, launch::BATCH>(occupancy);
+  return launch::prepare<fast::REC_DF, launch::BATCH>(occupancy);
 }
 
 cudaError_t launch_batch_mixed(const SweepParams& P, const BatchList& L, int axis, int eos,
                                cudaStream_t s) {
-  return launch::launch_batch<true>(P, L, axis, eos, s);
+  return launch::launch_batch<fast::REC_DF>(P, L, axis, eos, s);
 }
 
 }  // namespace shasta

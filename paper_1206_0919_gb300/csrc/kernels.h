@@ -10,15 +10,17 @@
 namespace shasta {
 
 // Fused sweep launchers, one per precision (sweep_f64.cu, sweep_f32.cu,
-// sweep_mixed.cu).  Return the launch error.
+// sweep_mixed.cu, sweep_mixed64.cu).  Return the launch error.
 cudaError_t launch_sweep_f64(const SweepParams& P, int axis, int eos, cudaStream_t s);
 cudaError_t launch_sweep_f32(const SweepParams& P, int axis, int eos, cudaStream_t s);
 cudaError_t launch_sweep_mixed(const SweepParams& P, int axis, int eos, cudaStream_t s);
+cudaError_t launch_sweep_mixed64(const SweepParams& P, int axis, int eos, cudaStream_t s);
 // Sets the shared-memory attribute of every FP32 / mixed sweep kernel and
 // reports resident warps per SM as [eos][axis][variant].  Call once per
 // device before the first launch (and before any stream capture).
 cudaError_t prepare_sweep_f32(int occupancy[3][3][2]);
 cudaError_t prepare_sweep_mixed(int occupancy[3][3][2]);
+cudaError_t prepare_sweep_mixed64(int occupancy[3][3][2]);
 int sweep_warps_per_block_f32();
 // FP32 sweeps without the antidiffusion stage (sweep_f32_noaf.cu), same
 // launch parameters and occupancy layout as the fused FP32 sweeps.
@@ -32,6 +34,7 @@ size_t split_scratch_floats(int nx, int ny, int nz);
 cudaError_t launch_sweep_split(const SweepParams& P, int axis, int eos, float* scratch,
                                float* half_q, float* half_r, cudaStream_t s);
 int sweep_warps_per_block_mixed();
+int sweep_warps_per_block_mixed64();
 // Batched FP32 / MIXED sweeps (one launch over the work list L, all along
 // `axis`); prepare_* as above for the batched kernels.
 cudaError_t prepare_batch_f32(int occupancy[3][3][2]);

@@ -6,11 +6,11 @@
 namespace shasta {
 
 cudaError_t prepare_sweep_f32_noaf(int occupancy[3][3][2]) {
-  return launch::prepare<false, launch::NOAF>(occupancy);
+  return launch::prepare<fast::REC_F32, launch::NOAF>(occupancy);
 }
 
 cudaError_t launch_sweep_f32_noaf(const SweepParams& P, int axis, int eos, cudaStream_t s) {
-  return launch::launch_single<false, launch::NOAF>(P, axis, eos, s);
+  return launch::launch_single<fast::REC_F32, launch::NOAF>(P, axis, eos, s);
 }
 
 }  // namespace shasta

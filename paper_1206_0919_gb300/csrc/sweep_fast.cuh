@@ -310,13 +310,62 @@ __device__ __forceinline__ float table_p32(const EosTable& T, float E, float M2)
   return tab32(T, fmaf(-M, v, E));
 }
 
-// Velocity along the sweep and pressure of one cell, FP32 (MIXED: D in
-// double-float).  mx, my, mz are the momenta, m1 the one along the sweep.
-// Returns 1 if |M| was clamped or E <= 0.
-template <int EOS, bool MIXED>
+// Recovery arithmetic of the kernels on a float state: REC_F32 all in
+// float (precision FP32); REC_DF |M|^2 and D = E^2 - |M|^2 in double-float,
+// the rest in float (MIXED); REC_F64 D, the root s, p and w in double from
+// the float state, rounded to float for the transport (MIXED_FP64).
+constexpr int REC_F32 = 0, REC_DF = 1, REC_F64 = 2;
+
+// REC_F64: velocity along the sweep and pressure of one cell, every
+// operation in double (IEEE division and square root) on the float state;
+// the same closed forms as rec32 below.  omd = 1 - delta in double.
+template <int EOS>
+__device__ __forceinline__ unsigned rec64(float Ef, float mxf, float myf, float mzf, float m1f,
+                                          double omd, double B, double ec, float& w, float& p) {
+  const double E = Ef, mx = mxf, my = myf, mz = mzf;
+  unsigned clamped = 0;
+  double M2 = fma(mx, mx, fma(my, my, mz * mz));
+  const double lim = omd * E;
+  const double L2 = lim * lim;
+  double m = m1f;
+  if (M2 > L2) {
+    m = m * (lim / sqrt(M2));
+    M2 = L2;
+    clamped = 1;
+  }
+  double D = fmax(fma(E, E, -M2), 0.0);
+  double pp;
+  if constexpr (EOS == EOS_BAG) {
+    const bool bag = 3.0 * D > ec * fma(2.0, E, ec);
+    const double b = bag ? B : 0.0;
+    const double q = fma(-4.0, b, E);
+    const double r = fma(3.0, D, fma(q, q, -12.0 * (b * b)));
+    const double s = sqrt(fmax(r, 0.0));
+    pp = fma(-(4.0 / 3.0) * b, E, D) / fma(-2.0, b, E + s) - (4.0 / 3.0) * b;
+    if (bag && !(E > ec && r >= 0.0 && fma(3.0, pp, 4.0 * B) > ec)) pp = M2 / (E - ec) - E;
+  } else {
+    const double s = sqrt(fma(3.0, D, E * E));
+    pp = D / (E + s);
+  }
+  w = (float)(m / (E + pp));
+  p = (float)pp;
+  if (!(E > 0.0)) {
+    w = 0.0f;
+    p = 0.0f;
+    clamped = 1;
+  }
+  return clamped;
+}
+
+// Velocity along the sweep and pressure of one cell, FP32 (REC_DF: D in
+// double-float; REC_F64: rec64).  mx, my, mz are the momenta, m1 the one
+// along the sweep.  Returns 1 if |M| was clamped or E <= 0.
+template <int EOS, int REC>
 __device__ __forceinline__ unsigned rec32(float E, float mx, float my, float mz, float m1,
-                                          float omd, float B, float ec, const EosTable& T,
-                                          float& w, float& p) {
+                                          float omd, double omd64, float B, float ec,
+                                          const EosTable& T, float& w, float& p) {
+  if constexpr (REC == REC_F64 && EOS != EOS_TABLE)
+    return rec64<EOS>(E, mx, my, mz, m1, omd64, B, ec, w, p);
   unsigned clamped = 0;
   float M2 = fmaf(mx, mx, fmaf(my, my, mz * mz));
   const float E2 = E * E;
@@ -330,7 +379,7 @@ __device__ __forceinline__ unsigned rec32(float E, float mx, float my, float mz,
     M2 = L2;
     D = E2 - M2;
     clamped = 1;
-  } else if (MIXED) {
+  } else if (REC == REC_DF) {
     // D = E^2 - |M|^2 with |M|^2 = hi + lo from error-free products and
     // compensated sums; E^2 - hi in one fused multiply-add (one rounding of
     // the exact difference), then lo
@@ -386,14 +435,15 @@ __device__ __forceinline__ unsigned rec32(float E, float mx, float my, float mz,
 // cell, hi: U^(n+1/2) four cells back): E, the three momenta and the
 // momentum along the sweep.  cnt counts the lo cell when in_seg (a cell of
 // the piece's own positions) and it was clamped or vacuum.
-template <int EOS, bool MIXED>
-__device__ __forceinline__ void rec2(f2 E, f2 mx, f2 my, f2 mz, f2 mpar, float omd, float B,
-                                     float ec, const EosTable& T, f2& w, f2& p, unsigned& cnt,
-                                     bool in_seg) {
+template <int EOS, int REC>
+__device__ __forceinline__ void rec2(f2 E, f2 mx, f2 my, f2 mz, f2 mpar, float omd, double omd64,
+                                     float B, float ec, const EosTable& T, f2& w, f2& p,
+                                     unsigned& cnt, bool in_seg) {
   float wl, wh, pl, ph;
-  const unsigned c = rec32<EOS, MIXED>(E.x, mx.x, my.x, mz.x, mpar.x, omd, B, ec, T, wl, pl);
+  const unsigned c =
+      rec32<EOS, REC>(E.x, mx.x, my.x, mz.x, mpar.x, omd, omd64, B, ec, T, wl, pl);
   if (c) cnt += in_seg ? 1u : 0u;
-  rec32<EOS, MIXED>(E.y, mx.y, my.y, mz.y, mpar.y, omd, B, ec, T, wh, ph);
+  rec32<EOS, REC>(E.y, mx.y, my.y, mz.y, mpar.y, omd, omd64, B, ec, T, wh, ph);
   w = f2{wl, wh};
   p = f2{pl, ph};
 }
@@ -563,7 +613,7 @@ using bc_ = std::integral_constant<bool, V>;
 // One piece of work: positions [s0, s1) of the 32 lines of line group g of
 // the event described by G (x path: s0 and, unless s1 = n, s1 on 8-cell
 // chunk boundaries).
-template <int EOS, int AXIS, bool MIXED, int RING, int DIST, bool AF, class Geo>
+template <int EOS, int AXIS, int REC, int RING, int DIST, bool AF, class Geo>
 __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, int g, int s0, int s1,
                                            float* wsm, int lane, unsigned& nclamp) {
   constexpr bool XP = AXIS == 0;
@@ -709,7 +759,7 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, i
       f2 w2, p2;
       // count each cell of the piece once (lanes past the last line only
       // repeat it)
-      rec2<EOS, MIXED>(E, mx, my, mz, mpar, omd, B, ec, P.tab, w2, p2, nclamp,
+      rec2<EOS, REC>(E, mx, my, mz, mpar, omd, P.omd, B, ec, P.tab, w2, p2, nclamp,
                        valid && (unsigned)(q - s0) < (unsigned)(s1 - s0));
       float pl, phi, pwl, pwh;
       up(w2, wn0, wh0);
@@ -864,7 +914,7 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, i
 // piece per line group it touches, each with its own halo); on the x path
 // range boundaries are moved down to 8-cell chunk boundaries of their line.
 // A batch may instead take whole line groups as work units (range_len 0).
-template <int EOS, int AXIS, bool MIXED, int WARPS, int RING, int DIST, bool BATCH, bool AF = true>
+template <int EOS, int AXIS, int REC, int WARPS, int RING, int DIST, bool BATCH, bool AF = true>
 __device__ __forceinline__ void sweep_items(const SweepParams& P, const BatchList& L) {
   constexpr bool XP = AXIS == 0;
   extern __shared__ __align__(16) float smem[];
@@ -903,7 +953,7 @@ __device__ __forceinline__ void sweep_items(const SweepParams& P, const BatchLis
       for (int r = first; r < total; r += nwarps) {
         const int k = entry(r);
         const GeoR G{geo_of<AXIS>(L.ev[L.idx[k]])};
-        sweep_item<EOS, AXIS, MIXED, RING, DIST, AF>(P, G, r - L.prefix[k], 0, G.n(), wsm, lane, nclamp);
+        sweep_item<EOS, AXIS, REC, RING, DIST, AF>(P, G, r - L.prefix[k], 0, G.n(), wsm, lane, nclamp);
         if (nclamp && G.g.clamp) atomicAdd(G.g.clamp, (unsigned long long)nclamp);
         nclamp = 0;
       }
@@ -923,7 +973,7 @@ __device__ __forceinline__ void sweep_items(const SweepParams& P, const BatchLis
         const int g = loc / n;
         const int s0 = loc - g * n;
         const int pe = min(end, x - s0 + n);  // the piece ends with the range or the line group
-        sweep_item<EOS, AXIS, MIXED, RING, DIST, AF>(P, G, g, s0, s0 + (pe - x), wsm, lane, nclamp);
+        sweep_item<EOS, AXIS, REC, RING, DIST, AF>(P, G, g, s0, s0 + (pe - x), wsm, lane, nclamp);
         if (nclamp && G.g.clamp) atomicAdd(G.g.clamp, (unsigned long long)nclamp);
         nclamp = 0;
         x = pe;
@@ -944,7 +994,7 @@ __device__ __forceinline__ void sweep_items(const SweepParams& P, const BatchLis
         const int g = x / n;
         const int s0 = x - g * n;
         const int pe = min(end, x - s0 + n);
-        sweep_item<EOS, AXIS, MIXED, RING, DIST, AF>(P, G, g, s0, s0 + (pe - x), wsm, lane, nclamp);
+        sweep_item<EOS, AXIS, REC, RING, DIST, AF>(P, G, g, s0, s0 + (pe - x), wsm, lane, nclamp);
         x = pe;
       }
     }
@@ -953,23 +1003,23 @@ __device__ __forceinline__ void sweep_items(const SweepParams& P, const BatchLis
 }
 
 // One event: the launch's work is that of P.
-template <int EOS, int AXIS, bool MIXED, int WARPS, int RING, int DIST, int MINB>
+template <int EOS, int AXIS, int REC, int WARPS, int RING, int DIST, int MINB>
 __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_fast_kernel(SweepParams P) {
-  sweep_items<EOS, AXIS, MIXED, WARPS, RING, DIST, false>(P, BatchList{});
+  sweep_items<EOS, AXIS, REC, WARPS, RING, DIST, false>(P, BatchList{});
 }
 
 // One event without the antidiffusion stage (the transport alone): an
 // ablation measuring what antidiffusion and limiter cost.
 template <int EOS, int AXIS, int WARPS, int RING, int DIST, int MINB>
 __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_noaf_kernel(SweepParams P) {
-  sweep_items<EOS, AXIS, false, WARPS, RING, DIST, false, false>(P, BatchList{});
+  sweep_items<EOS, AXIS, REC_F32, WARPS, RING, DIST, false, false>(P, BatchList{});
 }
 
 // A batch: the work of every event of the work list L, all swept along
 // AXIS; P supplies the batch's state arrays, eta and 1 - delta.
-template <int EOS, int AXIS, bool MIXED, int WARPS, int RING, int DIST, int MINB>
+template <int EOS, int AXIS, int REC, int WARPS, int RING, int DIST, int MINB>
 __global__ void __launch_bounds__(WARPS * 32, MINB) sweep_batch_kernel(SweepParams P, BatchList L) {
-  sweep_items<EOS, AXIS, MIXED, WARPS, RING, DIST, true>(P, L);
+  sweep_items<EOS, AXIS, REC, WARPS, RING, DIST, true>(P, L);
 }
 
 }  // namespace fast

@@ -5,11 +5,11 @@
 namespace shasta {
 
 cudaError_t prepare_sweep_mixed(int occupancy[3][3][2]) {
-  return launch::prepare<true, launch::SINGLE>(occupancy);
+  return launch::prepare<fast::REC_DF, launch::SINGLE>(occupancy);
 }
 
 cudaError_t launch_sweep_mixed(const SweepParams& P, int axis, int eos, cudaStream_t s) {
-  return launch::launch_single<true>(P, axis, eos, s);
+  return launch::launch_single<fast::REC_DF>(P, axis, eos, s);
 }
 
 int sweep_warps_per_block_mixed() { return launch::kWarps; }

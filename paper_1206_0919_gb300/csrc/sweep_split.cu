@@ -93,8 +93,8 @@ __global__ void k_recover(SweepParams P, St s, int axis, Ext X, float* w, float*
     float u[5];
     load(P, s, t, j, axis, u);
     float wv, pv;
-    c = fast::rec32<EOS, false>(u[0], u[1], u[2], u[3], u[1 + axis], float(P.omd), float(P.bag_B),
-                                float(P.bag_ec), P.tab, wv, pv);
+    c = fast::rec32<EOS, fast::REC_F32>(u[0], u[1], u[2], u[3], u[1 + axis], float(P.omd), P.omd,
+                                        float(P.bag_B), float(P.bag_ec), P.tab, wv, pv);
     w[X.at(j, t)] = wv;
     p[X.at(j, t)] = pv;
     c = count && j >= 0 && j < P.n ? c : 0u;

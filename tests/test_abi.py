@@ -62,7 +62,8 @@ def test_bad_scheme_is_rejected_before_any_device_call(lib):
     """Unknown schemes and the split scheme outside FP32 are option errors
     (EINVAL), found before the library looks for a device."""
     for kw in ({"scheme": 7}, {"scheme": "split", "precision": "fp64"},
-               {"scheme": "split", "precision": "mixed"}):
+               {"scheme": "split", "precision": "mixed"},
+               {"scheme": "split", "precision": "mixed_fp64"}, {"precision": 4}):
         with pytest.raises(S.ShastaError) as ei:
             S.Solver((4, 4, 4), **kw)
         assert ei.value.status == S.EINVAL, kw
@@ -79,6 +80,7 @@ def test_bad_eos_tables_are_rejected(lib):
            dict(table=np.arange(10) * 0.1 * 1.5, table_de=0.1),
            dict(table=np.where(np.arange(10) == 4, np.nan, good), table_de=0.1),
            dict(table=good, table_de=0.1, precision="mixed"),
+           dict(table=good, table_de=0.1, precision="mixed_fp64"),
            dict(table=good, table_de=0.1, scheme="no_antiflux")]
     for kw in bad:
         with pytest.raises(S.ShastaError) as ei:
@@ -103,9 +105,10 @@ def test_batch_and_server_without_gpu_fail_cleanly(lib):
     with pytest.raises(S.ShastaError) as ei:
         S.Server(1 << 30, staging_bytes=1 << 31)
     assert ei.value.status == S.EINVAL
-    with pytest.raises(S.ShastaError) as ei:
-        S.Batch(1 << 20, precision="fp64")
-    assert ei.value.status == S.EINVAL
+    for precision in ("fp64", "mixed_fp64"):  # batches run FP32 or MIXED
+        with pytest.raises(S.ShastaError) as ei:
+            S.Batch(1 << 20, precision=precision)
+        assert ei.value.status == S.EINVAL
 
 
 def test_null_handles_are_rejected(lib):
