@@ -126,8 +126,19 @@ typedef struct shasta_opts {
  * separate recovery, transport and antidiffusion kernels whose intermediate
  * results go through device memory (about 50 extra bytes of device memory
  * per cell); the method is the same, the rounding of a few differences is
- * not. */
-enum { SHASTA_SCHEME_FUSED = 0, SHASTA_SCHEME_NO_ANTIFLUX = 1, SHASTA_SCHEME_SPLIT = 2 };
+ * not.  TWO_SWEEPS (FP32; reflecting or periodic walls; ideal or bag EoS)
+ * blocks the first two sweeps of every step in time (the recompute-for-
+ * traffic trade of Sec. 3.1.4): one launch sweeps tiles of the plane of
+ * their two axes, with a 6-cell halo per side held in shared memory, along
+ * the first axis and then the second, so the state crosses device memory
+ * once for the two; the third sweep is the fused kernel.  Results are
+ * bitwise those of FUSED; single sweeps (shasta_sweep) use FUSED. */
+enum {
+  SHASTA_SCHEME_FUSED = 0,
+  SHASTA_SCHEME_NO_ANTIFLUX = 1,
+  SHASTA_SCHEME_SPLIT = 2,
+  SHASTA_SCHEME_TWO_SWEEPS = 3
+};
 
 typedef struct shasta_ctx shasta_ctx;
 

@@ -38,6 +38,7 @@ UNITS = [
     ("sweep_f32.cu", FAST),
     ("sweep_f32_noaf.cu", FAST),
     ("sweep_split.cu", FAST),
+    ("sweep_fuse2.cu", FAST),
     ("sweep_mixed.cu", FAST),
     ("sweep_mixed64.cu", FAST),
     ("batch_f32.cu", FAST),

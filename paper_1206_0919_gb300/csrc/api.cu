@@ -289,6 +289,25 @@ cudaError_t launch_sweep(shasta_ctx* c, int axis) {
   return e;
 }
 
+// The three sweeps of step phase ph (TWO_SWEEPS: the first two in one
+// launch, from the current buffer into the other).
+cudaError_t launch_step(shasta_ctx* c, int ph) {
+  const int* ax = kAxisTable + 3 * ph;
+  if (c->o.scheme == SHASTA_SCHEME_TWO_SWEEPS) {
+    SweepParams P = sweep_params(c, ax[0], c->cur, 0, 1);
+    cudaError_t e = launch_fuse2(P, c->g.nx, c->g.ny, c->g.nz, ax[0], ax[1], c->eos.kind,
+                                 c->sm_count, c->stream);
+    if (e != cudaSuccess) return e;
+    c->cur ^= 1;
+    return launch_sweep(c, ax[2]);
+  }
+  for (int sub = 0; sub < 3; ++sub) {
+    cudaError_t e = launch_sweep(c, ax[sub]);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 void drop_graph(shasta_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   c->graph = nullptr;
@@ -422,8 +441,16 @@ shasta_status shasta_create(const shasta_grid* g, double dx, double lambda, cons
   if (!(opts.eta >= 0.0 && opts.eta <= 0.5)) return fail(nullptr, SHASTA_EINVAL, "need 0 <= eta <= 0.5");
   if (!(opts.delta >= 0.0 && opts.delta < 0.5)) return fail(nullptr, SHASTA_EINVAL, "need 0 <= delta < 0.5");
   if (opts.scheme != SHASTA_SCHEME_FUSED && opts.scheme != SHASTA_SCHEME_NO_ANTIFLUX &&
-      opts.scheme != SHASTA_SCHEME_SPLIT)
+      opts.scheme != SHASTA_SCHEME_SPLIT && opts.scheme != SHASTA_SCHEME_TWO_SWEEPS)
     return fail(nullptr, SHASTA_EINVAL, "unknown scheme");
+  if (opts.scheme == SHASTA_SCHEME_TWO_SWEEPS) {
+    if (opts.precision != SHASTA_FP32)
+      return fail(nullptr, SHASTA_EINVAL, "the two-sweep scheme is FP32 only");
+    if (g->bc == SHASTA_BC_FROZEN)
+      return fail(nullptr, SHASTA_EINVAL, "the two-sweep scheme takes reflecting or periodic walls");
+    if (eos && eos->kind == SHASTA_EOS_TABLE)
+      return fail(nullptr, SHASTA_EINVAL, "the two-sweep scheme takes the closed-form EoS");
+  }
   if (opts.scheme == SHASTA_SCHEME_SPLIT && opts.precision != SHASTA_FP32)
     return fail(nullptr, SHASTA_EINVAL, "the split scheme is FP32 only");
   if (opts.delta == 0.0) opts.delta = opts.precision == SHASTA_FP64 ? 1e-10 : 1e-6;
@@ -562,6 +589,10 @@ shasta_status shasta_create(const shasta_grid* g, double dx, double lambda, cons
           : opts.scheme == SHASTA_SCHEME_NO_ANTIFLUX ? prepare_sweep_f32_noaf(c->occ)
                                                      : prepare_sweep_f32(c->occ);
     if (err != cudaSuccess) return bail(err, "prepare sweep kernels");
+    if (opts.scheme == SHASTA_SCHEME_TWO_SWEEPS) {
+      err = prepare_fuse2();
+      if (err != cudaSuccess) return bail(err, "prepare two-sweep kernels");
+    }
     c->wpb = opts.precision == SHASTA_MIXED        ? sweep_warps_per_block_mixed()
              : opts.precision == SHASTA_MIXED_FP64 ? sweep_warps_per_block_mixed64()
                                                    : sweep_warps_per_block_f32();
@@ -640,8 +671,7 @@ shasta_status shasta_step(shasta_ctx* c, int nsteps) {
         cudaGraph_t gr = nullptr;
         CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
         cudaError_t ce = cudaSuccess;
-        for (int s = 0; s < 6 && ce == cudaSuccess; ++s)
-          for (int sub = 0; sub < 3 && ce == cudaSuccess; ++sub) ce = launch_sweep(c, kAxisTable[3 * s + sub]);
+        for (int s = 0; s < 6 && ce == cudaSuccess; ++s) ce = launch_step(c, s);
         cudaError_t ce2 = cudaStreamEndCapture(c->stream, &gr);
         c->cur = 0;
         if (ce != cudaSuccess || ce2 != cudaSuccess) {
@@ -660,8 +690,7 @@ shasta_status shasta_step(shasta_ctx* c, int nsteps) {
       nsteps -= 6;
       continue;
     }
-    int ph = (int)(c->steps % 6);
-    for (int sub = 0; sub < 3; ++sub) CK(launch_sweep(c, kAxisTable[3 * ph + sub]), "sweep launch");
+    CK(launch_step(c, (int)(c->steps % 6)), "sweep launch");
     ++c->steps;
     --nsteps;
   }

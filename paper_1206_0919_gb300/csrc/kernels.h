@@ -34,6 +34,13 @@ size_t split_scratch_floats(int nx, int ny, int nz);
 cudaError_t launch_sweep_split(const SweepParams& P, int axis, int eos, float* scratch,
                                float* half_q, float* half_r, cudaStream_t s);
 int sweep_warps_per_block_mixed();
+// The first two sweeps of a step in one launch (sweep_fuse2.cu; FP32,
+// reflecting or periodic walls, ideal or bag EoS): along axis_a, then
+// axis_b, from P.qin/P.rin to P.qout/P.rout.  prepare_fuse2 sets the
+// kernels' shared-memory attribute (once per device, before any capture).
+cudaError_t prepare_fuse2();
+cudaError_t launch_fuse2(const SweepParams& P, int nx, int ny, int nz, int axis_a, int axis_b,
+                         int eos, int sm_count, cudaStream_t s);
 int sweep_warps_per_block_mixed64();
 // Batched FP32 / MIXED sweeps (one launch over the work list L, all along
 // `axis`); prepare_* as above for the batched kernels.

@@ -50,7 +50,7 @@ class Opts(C.Structure):
                 ("autotune", C.c_int), ("use_graphs", C.c_int), ("scheme", C.c_int)]
 
 
-SCHEMES = {"fused": 0, "no_antiflux": 1, "split": 2}
+SCHEMES = {"fused": 0, "no_antiflux": 1, "split": 2, "two_sweeps": 3}
 
 
 class BatchOpts(C.Structure):

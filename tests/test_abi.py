@@ -63,7 +63,10 @@ def test_bad_scheme_is_rejected_before_any_device_call(lib):
     (EINVAL), found before the library looks for a device."""
     for kw in ({"scheme": 7}, {"scheme": "split", "precision": "fp64"},
                {"scheme": "split", "precision": "mixed"},
-               {"scheme": "split", "precision": "mixed_fp64"}, {"precision": 4}):
+               {"scheme": "split", "precision": "mixed_fp64"}, {"precision": 4},
+               {"scheme": "two_sweeps", "precision": "fp64"},
+               {"scheme": "two_sweeps", "precision": "mixed"},
+               {"scheme": "two_sweeps", "bc": "frozen"}):
         with pytest.raises(S.ShastaError) as ei:
             S.Solver((4, 4, 4), **kw)
         assert ei.value.status == S.EINVAL, kw
@@ -81,7 +84,8 @@ def test_bad_eos_tables_are_rejected(lib):
            dict(table=np.where(np.arange(10) == 4, np.nan, good), table_de=0.1),
            dict(table=good, table_de=0.1, precision="mixed"),
            dict(table=good, table_de=0.1, precision="mixed_fp64"),
-           dict(table=good, table_de=0.1, scheme="no_antiflux")]
+           dict(table=good, table_de=0.1, scheme="no_antiflux"),
+           dict(table=good, table_de=0.1, scheme="two_sweeps")]
     for kw in bad:
         with pytest.raises(S.ShastaError) as ei:
             S.Solver((4, 4, 4), eos="table", **kw)
