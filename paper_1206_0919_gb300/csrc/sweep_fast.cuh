@@ -842,6 +842,11 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, i
       body(i, ic<1>{}, Gc, yb + YSLOT, yb4 + YSLOT, nullptr, wsm + ((r + 4) & 7) * YSLOT);
     }
   };
+  // steps actually needed: positions qs .. qe, in whole duos; the x path
+  // starts its first chunk at s0 - 6 (the sweep's reach), not at the chunk
+  // boundary below it
+  const int steps = ((qe - qs + 1) + 1) & ~1;
+  const int hbeg0 = ((s0 - 2 * NG) - qs) & ~1;
 
   int fl = s0;  // x path: next output position to write back
 #pragma unroll 1
@@ -858,8 +863,10 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, i
         x_issue(C + 1, true);
       cp_commit();
     }
+    // the last block stops after the last needed duo
+    const int hend = min(8, steps - i0);
 #pragma unroll 1
-    for (int h = 0; h < 8; h += 2) {
+    for (int h = i0 == 0 ? hbeg0 : 0; h < hend; h += 2) {
       if (steady)
         duo(i0 + h, bc_<false>{});
       else
