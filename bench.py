@@ -51,7 +51,7 @@ def parse():
                     help="timed steps; the headline workload's step is one 200-step event")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "mixed", "fp64"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "mixed", "mixed_fp64", "fp64"], default="fp32")
     ap.add_argument("--grid", type=int, default=N_GRID)
     ap.add_argument("--e2e-events", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -484,7 +484,8 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "mixed": "f32+f64", "fp64": "f64"}[args.precision],
+            "dtype": {"fp32": "f32", "mixed": "f32+f64", "mixed_fp64": "f32+f64",
+                      "fp64": "f64"}[args.precision],
             "data": "synthetic", "config": cfg,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             # per event: 600 sweeps, the input check and five conversions
@@ -658,7 +659,7 @@ def run_batch(args):
         raise RuntimeError("bench.py needs a CUDA device (no CPU fallback exists)")
     torch.cuda.set_device(local)
     ranks = Ranks("nccl", torch.device("cuda", local))
-    precision = args.precision if args.precision != "fp64" else "mixed"
+    precision = "fp32" if args.precision == "fp32" else "mixed"  # batches run FP32 or MIXED
     args.events = args.events or 64
     evs = W.batch_events(n_events=args.events, seed=3 + 1000 * rank)
     total = sum(ev["N"] ** 3 for ev in evs)
@@ -811,7 +812,7 @@ def serve_stream_leg(ranks, local, inputs, rate, n_events, precision, budget_gb=
 def serve_legs(args, ranks, local, rates=(60.0, 200.0), n_events=150):
     """Config 4 on the headline line: short Poisson streams at each rate."""
     inputs = serve_inputs()
-    precision = args.precision if args.precision not in ("fp64",) else "fp32"
+    precision = "mixed" if args.precision == "mixed" else "fp32"  # servers run FP32 or MIXED
     out = {"workload": "serve_poisson",
            "sizes": "N in {64,96,128,192} with probabilities 0.4/0.3/0.2/0.1, grids N^3",
            "eos": "alternating: ideal p=e/3 / bag (B=0.1, e_c=0.5)", "steps_per_event": 150,
@@ -831,7 +832,7 @@ def run_serve(args):
         raise RuntimeError("bench.py needs a CUDA device (no CPU fallback exists)")
     torch.cuda.set_device(local)
     ranks = Ranks("nccl", torch.device("cuda", local))
-    precision = args.precision if args.precision != "fp64" else "fp32"
+    precision = "mixed" if args.precision == "mixed" else "fp32"  # servers run FP32 or MIXED
     args.events = args.events or 300
     leg = serve_stream_leg(ranks, local, serve_inputs(), args.rate, args.events, precision,
                            budget_gb=args.budget_gb, max_resident=args.max_resident,
