@@ -623,6 +623,8 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, i
   const long long t = (long long)g * LANES + lane;
   const bool valid = t < G.plane();
   const long long tl = valid ? t : G.plane() - 1;
+  // cells of the piece this lane owns: q - s0 in [0, span) (none past the last line)
+  const unsigned span = valid ? (unsigned)(s1 - s0) : 0u;
   const long long base = G.off() + (tl % G.nb()) * G.sb() + (tl / G.nb()) * G.sc();  // first cell of the line
   // positions streamed: qs .. qe (the x path starts on a chunk boundary)
   const int qs = XP ? ((s0 - 2 * NG) & ~(CH - 1)) : s0 - 2 * NG;
@@ -760,7 +762,7 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, i
       // count each cell of the piece once (lanes past the last line only
       // repeat it)
       rec2<EOS, REC>(E, mx, my, mz, mpar, omd, P.omd, B, ec, P.tab, w2, p2, nclamp,
-                       valid && (unsigned)(q - s0) < (unsigned)(s1 - s0));
+                       (unsigned)(q - s0) < span);
       float pl, phi, pwl, pwh;
       up(w2, wn0, wh0);
       up(p2, pl, phi);
@@ -807,7 +809,7 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, i
     const int jo = q - LAG;
     if (XP) {
       // the ring entry of position jo is dead: stage the result there
-      if (jo >= s0 && jo < s1) {
+      if ((unsigned)(jo - s0) < (unsigned)(s1 - s0)) {
         const int pj = jo & 7;
         float o0, o1, o2, o3;
         up(oA, o0, o1);
@@ -815,7 +817,7 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, i
         *reinterpret_cast<float4*>(sjo + lane * XQSTR + pj * 4) = make_float4(o0, o1, o2, o3);
         sjo[XQ + lane * XRSTR + pj] = oR;
       }
-    } else if (valid && jo >= s0 && jo < s1) {
+    } else if ((unsigned)(jo - s0) < span) {
       const unsigned c = base32 + (unsigned)jo * stride32;
       float o0, o1, o2, o3;
       up(oA, o0, o1);
