@@ -189,16 +189,17 @@ shasta_status shasta_step(shasta_ctx* ctx, int nsteps);
  * time or study one sweep.  Errors: EINVAL (bad axis, state never set), ECUDA. */
 shasta_status shasta_sweep(shasta_ctx* ctx, int axis);
 
-/* Times the launch choices of the FP32 / MIXED sweep kernels for this grid
- * (work range length, register variant) and keeps the fastest per axis.  A
- * sweep's positions (line groups of 32 lines x positions along the axis) are
- * cut into equal ranges handed to the resident warps.
+/* Times the launch choices of the sweep kernels for this grid and keeps the
+ * fastest per axis.  FP32 / MIXED: work range length and register variant (a
+ * sweep's positions, line groups of 32 lines x positions along the axis, are
+ * cut into equal ranges handed to the resident warps).  FP64: the length of
+ * the line segments streamed one per thread.  No choice changes results.
  * Runs sweeps from the current state into the spare buffer only, so the
  * state is unchanged; synchronous.  Errors: EINVAL (state not set), ECUDA. */
 shasta_status shasta_autotune(shasta_ctx* ctx);
 
-/* Current launch choice per axis: out[2a] = register variant, out[2a+1] =
- * positions per work range (FP64: unused). */
+/* Current launch choice per axis: out[2a] = register variant (FP64: 0),
+ * out[2a+1] = positions per work range (FP64: cells per line segment). */
 shasta_status shasta_get_tuning(const shasta_ctx* ctx, int out[6]);
 
 /* Waits until all work enqueued on the context's stream has finished. */

@@ -232,18 +232,8 @@ SweepParams sweep_params(shasta_ctx* c, int axis, int from, int variant, long lo
   P.bag_ec = c->eos.e_c;
   P.clamp_count = c->d_count;
   P.tab = c->tab;
-  P.range_len = range < 1 ? 1 : range;
+  P.range_len = range < 1 ? 1 : range;  // FP64: cells per line segment
   P.variant = variant;
-  if (c->o.precision == SHASTA_FP64) {
-    // one thread per line segment: about 1024 threads per SM, segments of
-    // at least 16 cells (each re-reads a 6-cell halo per side)
-    const long long want = (long long)c->sm_count * 1024;
-    long long nseg = (want + P.plane - 1) / P.plane;
-    const long long cap = P.n / 16 > 1 ? P.n / 16 : 1;
-    nseg = nseg < 1 ? 1 : (nseg > cap ? cap : nseg);
-    P.range_len = (P.n + nseg - 1) / nseg;
-    if (c->force_range > 0) P.range_len = c->force_range;  // environment override
-  }
   if (c->o.precision != SHASTA_FP64) {
     // at most one wave of resident warps loops over the ranges
     const long long total = work_positions(c, axis);
@@ -256,10 +246,29 @@ SweepParams sweep_params(shasta_ctx* c, int axis, int from, int variant, long lo
   return P;
 }
 
-// Launch choice of the FP32 / MIXED kernels for an axis: environment
-// overrides, else the autotuned choice, else variant 0 and one range per
-// resident warp.
+// FP64 kernel: one thread per line segment; default segment length for
+// about 1024 threads per SM, segments of at least 16 cells (each re-runs a
+// 6-cell halo per side).
+long long fp64_segment(const shasta_ctx* c, int axis) {
+  const long long n = axis == 0 ? c->g.nx : (axis == 1 ? c->g.ny : c->g.nz);
+  const long long plane = (long long)c->g.nx * c->g.ny * c->g.nz / (n > 0 ? n : 1);
+  const long long want = (long long)c->sm_count * 1024;
+  long long nseg = (want + plane - 1) / (plane > 0 ? plane : 1);
+  const long long cap = n / 16 > 1 ? n / 16 : 1;
+  nseg = nseg < 1 ? 1 : (nseg > cap ? cap : nseg);
+  return (n + nseg - 1) / nseg;
+}
+
+// Launch choice for an axis: environment overrides, else the autotuned
+// choice, else variant 0 and one range per resident warp (FP32 / MIXED) or
+// the default segment length (FP64).
 void launch_choice(const shasta_ctx* c, int axis, int& variant, long long& range) {
+  if (c->o.precision == SHASTA_FP64) {
+    variant = 0;
+    range = c->tuned && c->tune_range[axis] > 0 ? c->tune_range[axis] : fp64_segment(c, axis);
+    if (c->force_range > 0) range = c->force_range;
+    return;
+  }
   variant = c->tuned ? c->tune_var[axis] : 0;
   if (c->force_variant >= 0) variant = c->force_variant;
   const long long warps = (long long)c->sm_count * c->occ[c->eos.kind][axis][variant];
@@ -313,13 +322,28 @@ void drop_graph(shasta_ctx* c) {
   c->graph = nullptr;
 }
 
+// Mean time of `reps` sweeps of axis with parameters P (after `warm`
+// untimed ones), from the current buffer into the other one.
+cudaError_t time_choice(shasta_ctx* c, int axis, const SweepParams& P, int warm, int reps,
+                        cudaEvent_t e0, cudaEvent_t e1, float& ms) {
+  cudaError_t ce = cudaSuccess;
+  for (int r = 0; r < warm && ce == cudaSuccess; ++r) ce = launch_params(c, axis, P);
+  if (ce == cudaSuccess) ce = cudaEventRecord(e0, c->stream);
+  for (int r = 0; r < reps && ce == cudaSuccess; ++r) ce = launch_params(c, axis, P);
+  if (ce == cudaSuccess) ce = cudaEventRecord(e1, c->stream);
+  if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+  if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+  return ce;
+}
+
 // Times candidate launch choices per axis with repeated sweeps from the
 // current buffer into the other one (the state itself is not changed) and
-// keeps the fastest: the register variant, and ranges of one line group
-// (no line is cut) or of 1/4 .. 3 ranges per resident warp.  The choice
-// does not change results.
+// keeps the fastest.  FP32 / MIXED: the register variant, and ranges of one
+// line group (no line is cut) or of 1/4 .. 3 ranges per resident warp.
+// FP64: the line segment length (the default one, 24 .. 128 cells, whole
+// lines).  The choice does not change results.
 shasta_status autotune(shasta_ctx* c) {
-  if (c->o.precision == SHASTA_FP64 || c->o.scheme == SHASTA_SCHEME_SPLIT) {
+  if (c->o.scheme == SHASTA_SCHEME_SPLIT) {
     c->tuned = true;
     return SHASTA_OK;
   }
@@ -327,34 +351,40 @@ shasta_status autotune(shasta_ctx* c) {
   CK(cudaEventCreate(&e0), "cudaEventCreate");
   CK(cudaEventCreate(&e1), "cudaEventCreate");
   shasta_status st = SHASTA_OK;
+  const bool f64 = c->o.precision == SHASTA_FP64;
   static const double shares[] = {0.25, 0.5, 1.0, 2.0, 3.0};
+  static const long long segments[] = {24, 32, 48, 64, 100, 128};
   for (int axis = 0; axis < 3 && st == SHASTA_OK; ++axis) {
     const int n = axis == 0 ? c->g.nx : (axis == 1 ? c->g.ny : c->g.nz);
     const long long total = work_positions(c, axis);
     float best = 1e30f;
     int bv = 0;
-    long long br = n;
-    for (int var = 0; var < 2; ++var) {
-      const long long warps = (long long)c->sm_count * c->occ[c->eos.kind][axis][var];
-      long long cands[6];
+    long long br = f64 ? fp64_segment(c, axis) : n;
+    for (int var = 0; var < (f64 ? 1 : 2); ++var) {
+      long long cands[8];
       int nc = 0;
-      cands[nc++] = n;
-      for (double sh : shares) {
-        const long long r = range_for(total, warps, sh);
+      auto add = [&](long long r) {
         bool dup = false;
         for (int i = 0; i < nc; ++i) dup = dup || cands[i] == r;
-        if (!dup && r < total) cands[nc++] = r;
+        if (!dup) cands[nc++] = r;
+      };
+      if (f64) {
+        add(fp64_segment(c, axis));
+        for (long long r : segments)
+          if (r < n) add(r);
+        add(n);
+      } else {
+        const long long warps = (long long)c->sm_count * c->occ[c->eos.kind][axis][var];
+        add(n);
+        for (double sh : shares) {
+          const long long r = range_for(total, warps, sh);
+          if (r < total) add(r);
+        }
       }
       for (int ci = 0; ci < nc && st == SHASTA_OK; ++ci) {
-        SweepParams P = sweep_params(c, axis, c->cur, var, cands[ci]);
-        cudaError_t ce = cudaSuccess;
-        for (int r = 0; r < 2 && ce == cudaSuccess; ++r) ce = launch_params(c, axis, P);
-        if (ce == cudaSuccess) ce = cudaEventRecord(e0, c->stream);
-        for (int r = 0; r < 4 && ce == cudaSuccess; ++r) ce = launch_params(c, axis, P);
-        if (ce == cudaSuccess) ce = cudaEventRecord(e1, c->stream);
-        if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
         float ms = 0;
-        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+        const cudaError_t ce = time_choice(c, axis, sweep_params(c, axis, c->cur, var, cands[ci]),
+                                           f64 ? 1 : 2, f64 ? 2 : 4, e0, e1, ms);
         if (ce != cudaSuccess) {
           st = cuda_fail(c, ce, "autotune");
           break;

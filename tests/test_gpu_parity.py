@@ -301,11 +301,14 @@ def test_graphs_and_launch_choices_bitwise(monkeypatch, precision):
             assert np.array_equal(a, b)
 
 
-def test_autotune_keeps_state():
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_autotune_keeps_state(precision):
+    """The autotuner leaves the state alone and picks a valid choice per axis
+    (FP64: one of its segment lengths, at most the line)."""
     shape = (64, 48, 40)
     pr = W.hot_spots(shape=shape, seed=22, n_spots=4)
     U0 = oracle().prim2cons(OR.params(shape), *pr.as_list())
-    with S.Solver(shape, precision="fp32", autotune=False) as s:
+    with S.Solver(shape, precision=precision, autotune=False) as s:
         s.set_conserved(U0)
         before = s.get_conserved()
         s.autotune()
@@ -313,7 +316,10 @@ def test_autotune_keeps_state():
         tune = s.tuning()
     for a, b in zip(before, after):
         assert np.array_equal(a, b)
-    assert all(v in (0, 1) and r >= 1 for v, r in tune)
+    if precision == "fp64":
+        assert all(v == 0 and 1 <= r <= n for (v, r), n in zip(tune, shape))
+    else:
+        assert all(v in (0, 1) and r >= 1 for v, r in tune)
 
 
 def single_precision_yardstick(P, U0, nsteps, ref_e):
