@@ -354,6 +354,7 @@ def run_ours(args):
     solver.set_primitives(*prims.as_list())
     U0 = [torch.empty((N, N, N), dtype=torch.float64, device="cuda") for _ in range(5)]
     solver.get_conserved(U0)
+    tot0 = solver.totals()  # conserved totals of the state the solver holds
 
     def event(marks=None):
         """One benchmark step: the event from its initial state (set through
@@ -395,6 +396,9 @@ def run_ours(args):
     sweep_ms = ranks.max(sum(a.elapsed_time(b) for a, b in marks))
     units = ncell * EVENT_STEPS * args.steps  # cell-updates of one rank
     value = job_rate(world, units, ms / 1e3)
+    # the last timed event's result: e after its 200 steps and the totals
+    e_final = solver.get_primitives()["e"] if rank == 0 and not args.no_fp64_path else None
+    tot1 = solver.totals()
 
     # roofline of the sweep kernel (three launches per split step)
     word = 8 if args.precision == "fp64" else 4
@@ -459,7 +463,6 @@ def run_ours(args):
            "events": args.e2e_events}
     solver2.close()
     solver.close()
-    del U0
 
     extra = {}
     if not args.no_fp64_path and args.precision != "fp64":
@@ -477,6 +480,8 @@ def run_ours(args):
             r64 = ncell * k64 / (e0.elapsed_time(e1) / 1e3)
         extra["fp64_path"] = {"value": r64, "unit": UNIT,
                               "speedup_of_value": value / world / r64}
+        if e_final is not None:
+            extra["accuracy"] = accuracy_leg(args, stream, local, U0, e_final, tot0, tot1)
     if not args.no_legs:
         extra["precisions"] = precision_legs(args, stream, local, prims, value / world)
         extra["alu_peaks"] = alu_peaks(local, stream)
@@ -484,6 +489,7 @@ def run_ours(args):
                                      steps=100, warmup=12)
         extra["serve"] = serve_legs(args, ranks, local, rates=(60.0, 200.0), n_events=150)
 
+    del U0
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, threads, steps, t = oracle_rate(N)
@@ -512,6 +518,39 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
     ranks.close()
     return 0
+
+
+def accuracy_leg(args, stream, local, U0, e_final, tot0, tot1):
+    """Error of the benchmarked event's result against FP64: relative L1
+    distance of e after the event's 200 steps from the plain FP64 GPU path
+    (which equals the FP64 oracle to 1e-12 per cell in the parity tests)
+    run from the same float32-rounded state at the same clamp margin, beside
+    the single-precision yardstick stored for this workload (the oracle's
+    algorithm in single precision against itself in double) and the drift
+    of the conserved totals E and R (reflecting walls conserve both)."""
+    import numpy as np
+
+    from paper_1206_0919_gb300 import shasta as S
+
+    N = args.grid
+    with S.Solver((N, N, N), precision="fp64", delta=1e-6, stream=stream.cuda_stream,
+                  device=local) as s64:
+        s64.set_conserved([u.float().double() for u in U0])
+        s64.step(EVENT_STEPS)
+        e64 = s64.get_primitives()["e"]
+    err = float(np.abs(e_final - e64).sum() / np.abs(e64).sum())
+    yard = None
+    path = os.path.join(ROOT, "tests", "golden", "sensitivity.json")
+    if N == 200 and args.precision in ("fp32", "mixed", "mixed_fp64") and os.path.exists(path):
+        with open(path) as f:
+            yard = json.load(f)["hot_spots_200"]["single_precision"]["max"].get(str(EVENT_STEPS))
+    drift = {k: float(abs(tot1[i] - tot0[i]) / abs(tot0[i])) for k, i in (("E", 0), ("R", 4))}
+    return {"rel_l1_e": err, "steps": EVENT_STEPS,
+            "against": "plain FP64 GPU path from the float32-rounded initial state, "
+                       "clamp margin 1e-6",
+            "single_precision_yardstick": yard,
+            "ratio_to_yardstick": err / yard if yard else None,
+            "totals_drift": drift}
 
 
 def precision_legs(args, stream, local, prims, fp32_rate, k=30):

@@ -1,7 +1,8 @@
 """The benchmark's headline line on a GPU: one JSON line with the contract's
 keys, the roofline of the sweep kernel, the end-to-end figure through the
 public API, the clocks, and the batched, serving, precision and ALU-peak
-legs, each with plausible values (a short run: one timed event)."""
+legs, each with plausible values, and the event's error against FP64 (a
+short run: one timed event)."""
 import json
 import os
 import subprocess
@@ -51,3 +52,9 @@ def test_headline_line_keys_and_legs():
     a = d["alu_peaks"]
     assert a["fp32"]["tflops"] > 10 * a["fp64"]["tflops"] > 0
     assert d["fp64_path"]["speedup_of_value"] > 10
+    # the event's error against FP64 after its 200 steps, within twice the
+    # single-precision yardstick, and the drift of the conserved totals
+    acc = d["accuracy"]
+    assert acc["steps"] == 200 and acc["single_precision_yardstick"] > 0
+    assert 0 < acc["rel_l1_e"] <= 2 * acc["single_precision_yardstick"]
+    assert acc["totals_drift"]["E"] <= 1e-5 and acc["totals_drift"]["R"] <= 1e-5
