@@ -520,6 +520,50 @@ def run_ours(args):
     return 0
 
 
+def fp64_reference_e(N, prims, nsteps, stream, local, eos="ideal"):
+    """e after `nsteps` steps of the plain FP64 GPU path (equal to the FP64
+    oracle to 1e-12 per cell in the parity tests) from the float32-rounded
+    conserved state of the primitive arrays `prims`, at the FP32 clamp margin:
+    the reference a single-precision result of the same input is held to.
+    Also returns the flow's sensitivity: the relative L1 distance of e when
+    the same path starts from a seeded one-ulp perturbation of that float32
+    state (what rounding-size input differences alone grow into)."""
+    from paper_1206_0919_gb300 import shasta as S
+    from paper_1206_0919_gb300 import workloads as W
+
+    def run(U):
+        with S.Solver((N, N, N), precision="fp64", delta=1e-6, eos=eos, check_input=False,
+                      stream=stream.cuda_stream, device=local) as s64:
+            s64.set_conserved(U)
+            s64.step(nsteps)
+            return s64.get_primitives()["e"]
+
+    with S.Solver((N, N, N), precision="fp64", eos=eos, stream=stream.cuda_stream,
+                  device=local) as s64:
+        s64.set_primitives(*prims)
+        U = s64.get_conserved()
+    ref = run(W.rounded_to_single(U))
+    return ref, rel_l1(run(W.ulp_flips(U, 1)), ref)
+
+
+def rel_l1(a, ref):
+    import numpy as np
+
+    return float(np.abs(a - ref).sum() / np.abs(ref).sum())
+
+
+def accuracy_summary(errs, steps):
+    """Per-event errors against FP64 with the largest, and the largest ratio
+    of an event's error to its own one-ulp sensitivity."""
+    return {"events": errs, "max_rel_l1_e": max(v["rel_l1_e"] for v in errs.values()),
+            "max_ratio_to_spread": max(v["rel_l1_e"] / max(v["fp64_ulp_flip_spread"], 1e-300)
+                                       for v in errs.values()),
+            "steps": steps,
+            "against": "plain FP64 GPU path from the float32-rounded initial state, "
+                       "clamp margin 1e-6; spread: the same path from a seeded one-ulp "
+                       "perturbation of that state"}
+
+
 def accuracy_leg(args, stream, local, U0, e_final, tot0, tot1):
     """Error of the benchmarked event's result against FP64: relative L1
     distance of e after the event's 200 steps from the plain FP64 GPU path
@@ -692,7 +736,17 @@ def batch_leg(ranks, stream, local, n_events=64, precision="mixed", steps=100, w
 
     evs = W.batch_events(n_events=n_events, seed=3 + 1000 * ranks.rank)
     host = [W.event_prims(ev).as_list() for ev in evs]
-    leg, b, _ = _batch_timed(ranks, stream, local, evs, host, precision, steps, warmup)
+    leg, b, ids = _batch_timed(ranks, stream, local, evs, host, precision, steps, warmup)
+    if ranks.rank == 0:
+        # error against FP64 of the smallest, the median and the largest event
+        order = sorted(range(len(evs)), key=lambda i: evs[i]["N"])
+        errs = {}
+        for i in sorted({order[0], order[len(order) // 2], order[-1]}):
+            e_b = b.get_primitives(ids[i])["e"]
+            ref, spread = fp64_reference_e(evs[i]["N"], host[i], warmup + steps, stream, local)
+            errs[f"event{i}_N{evs[i]['N']}"] = {"rel_l1_e": rel_l1(e_b, ref),
+                                                "fp64_ulp_flip_spread": spread}
+        leg["accuracy"] = accuracy_summary(errs, warmup + steps)
     b.close()
     leg["workload"] = f"batch_{n_events}_events"
     leg["sizes"] = "N uniform in {48,64,96,128,160}, grids N^3, 5-40 hot spots, v_r = 0.1 r/R_box"
@@ -812,10 +866,13 @@ def serve_inputs():
 
 
 def serve_stream_leg(ranks, local, inputs, rate, n_events, precision, budget_gb=48.0,
-                     max_resident=64, steps_per_round=6, warmup=3):
+                     max_resident=64, steps_per_round=6, warmup=3, accuracy=False):
     """One Poisson stream (every world-th event per rank, `rate` arrivals
-    per second per rank) replayed in real time against a fresh server."""
+    per second per rank) replayed in real time against a fresh server.
+    accuracy: also the error against FP64 of the first served event of each
+    (N, EoS) with N in {64, 128}."""
     import numpy as np
+    import torch
 
     from paper_1206_0919_gb300 import serving
     from paper_1206_0919_gb300 import shasta as S
@@ -832,11 +889,16 @@ def serve_stream_leg(ranks, local, inputs, rate, n_events, precision, budget_gb=
             for i in range(max(1, warmup))]
     serving.replay(srv, warm, inputs)
     st0 = srv.stats()
+    picked = {}
+    for i, ev in enumerate(stream):
+        if accuracy and ev["N"] in (64, 128) and (ev["N"], ev["eos"]) not in picked:
+            picked[(ev["N"], ev["eos"])] = i
+    keep = set(picked.values())
     sampler = ClockSampler(local)
     sampler.start()
     ranks.barrier()
     t_wall0 = time.time()
-    recs = serving.replay(srv, stream, inputs)
+    recs = serving.replay(srv, stream, inputs, keep=keep.__contains__)
     t_wall1 = time.time()
     sampler.stop()
     st1 = srv.stats()
@@ -846,6 +908,18 @@ def serve_stream_leg(ranks, local, inputs, rate, n_events, precision, budget_gb=
     lat_sub = ranks.gather([r["t_done"] - r["t_submit"] for r in recs])
     cells = sum(ranks.gather([sum(r["N"] ** 3 * r["steps"] for r in recs)]))
     a, b = serving.summary(lat_arr), serving.summary(lat_sub)
+    acc = None
+    if keep:
+        ts = torch.cuda.Stream()
+        errs = {}
+        for r in recs:
+            if "e" in r:
+                ev = stream[r["i"]]
+                ref, spread = fp64_reference_e(ev["N"], inputs(ev), r["steps"], ts, local,
+                                               eos=ev["eos"])
+                errs[f"event{r['i']}_N{ev['N']}_{ev['eos']}"] = {
+                    "rel_l1_e": rel_l1(r["e"], ref), "fp64_ulp_flip_spread": spread}
+        acc = accuracy_summary(errs, stream[0]["steps"]) if errs else None
     return {
         "value": len(lat_arr) / span, "unit": "events/s", "events": len(lat_arr),
         "offered_events_per_s": rate * ranks.world, "span_s": span,
@@ -860,6 +934,7 @@ def serve_stream_leg(ranks, local, inputs, rate, n_events, precision, budget_gb=
                                 "d2h": int(np.mean([48 * r["N"] ** 3 for r in recs]))},
         "gpu_launches": int(st1["sweep_launches"] - st0["sweep_launches"]),
         "clocks": sampler.summary(t_wall0, t_wall1),
+        "accuracy": acc,
     }
 
 
@@ -872,7 +947,8 @@ def serve_legs(args, ranks, local, rates=(60.0, 200.0), n_events=150):
            "eos": "alternating: ideal p=e/3 / bag (B=0.1, e_c=0.5)", "steps_per_event": 150,
            "precision": precision, "events_per_stream": n_events * ranks.world}
     for rate in rates:
-        out[f"{rate:g}_per_s"] = serve_stream_leg(ranks, local, inputs, rate, n_events, precision)
+        out[f"{rate:g}_per_s"] = serve_stream_leg(ranks, local, inputs, rate, n_events, precision,
+                                                  accuracy=ranks.rank == 0 and rate == rates[-1])
     return out
 
 
@@ -890,7 +966,8 @@ def run_serve(args):
     args.events = args.events or 300
     leg = serve_stream_leg(ranks, local, serve_inputs(), args.rate, args.events, precision,
                            budget_gb=args.budget_gb, max_resident=args.max_resident,
-                           steps_per_round=args.steps_per_round, warmup=args.warmup)
+                           steps_per_round=args.steps_per_round, warmup=args.warmup,
+                           accuracy=rank == 0)
     if rank == 0:
         out = {
             "metric": METRIC, "value": leg["value"], "unit": "events/s", "n_gpus": world,
@@ -910,7 +987,7 @@ def run_serve(args):
                     "step": "one event (mean bytes): host arrays in, 150 steps, primitives "
                             "to host buffers"},
             "gpu_launches": leg["gpu_launches"], "clocks": leg["clocks"], "roofline": None,
-            "cpu_baseline": None,
+            "cpu_baseline": None, "accuracy": leg["accuracy"],
         }
         print(json.dumps(out), flush=True)
     ranks.close()

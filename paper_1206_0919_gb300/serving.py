@@ -34,14 +34,17 @@ def gather(values, dist=None):
     return [v for p in parts for v in p]
 
 
-def replay(server, events, inputs, poll_every=0.001, retry_sleep=0.0005, timeout=600.0):
+def replay(server, events, inputs, poll_every=0.001, retry_sleep=0.0005, timeout=600.0,
+           keep=None):
     """Submits `events` (dicts with t_arrival, N, eos, steps) at their
     arrival times, measured from the call, and polls until all have
     finished.  inputs(ev) gives the five primitive arrays of an event.
 
     Returns one record per event: arrival and submit times and the server's
     timings, all on the server's clock, plus the number of EAGAIN refusals
-    the client met (the queue was full) before the event was accepted."""
+    the client met (the queue was full) before the event was accepted.
+    keep(i), if given, picks the events whose result e is kept in the record
+    (key "e"); the others' results are dropped once polled."""
     clock0 = server.clock()
     wall0 = time.perf_counter()
     pending, records = {}, []
@@ -63,19 +66,19 @@ def replay(server, events, inputs, poll_every=0.001, retry_sleep=0.0005, timeout
                     if getattr(e, "status", None) != 3:
                         raise
                     refusals += 1
-                    _poll(server, pending, records)
+                    _poll(server, pending, records, keep)
                     time.sleep(retry_sleep)
             pending[t] = {"i": i, "N": N, "eos": ev["eos"], "refusals": refusals,
                           "t_arrival": clock0 + ev["t_arrival"]}
             i += 1
             continue
-        _poll(server, pending, records)
+        _poll(server, pending, records, keep)
         time.sleep(poll_every)
     records.sort(key=lambda r: r["i"])
     return records
 
 
-def _poll(server, pending, records):
+def _poll(server, pending, records, keep=None):
     for t in list(pending):
         r = server.poll(t)
         if r is None:
@@ -83,4 +86,6 @@ def _poll(server, pending, records):
         rec = pending.pop(t)
         rec.update(t_submit=r["t_submit"], t_admit=r["t_admit"], t_done=r["t_done"],
                    steps=r["steps"])
+        if keep is not None and keep(rec["i"]) and "prims" in r:
+            rec["e"] = r["prims"]["e"]
         records.append(rec)

@@ -43,6 +43,12 @@ def test_headline_line_keys_and_legs():
         assert k in d["clocks"], k
     b = d["batch64"]
     assert b["events"] == 64 and b["value"] > 1e9 and 0.05 < b["roofline"]["frac"] < 1.2
+    # sampled events against FP64, beside their own one-ulp sensitivity (the
+    # single-precision algorithm itself runs 2-30x its one-ulp spread)
+    for acc in (b["accuracy"], d["serve"]["200_per_s"]["accuracy"]):
+        assert len(acc["events"]) >= 3
+        assert all(v["fp64_ulp_flip_spread"] > 0 for v in acc["events"].values())
+        assert 0 < acc["max_ratio_to_spread"] < 100 and acc["max_rel_l1_e"] < 0.05
     for rate in ("60_per_s", "200_per_s"):
         s = d["serve"][rate]
         assert s["events"] == 150 and s["value"] > 1.0
