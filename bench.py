@@ -728,6 +728,18 @@ def _batch_timed(ranks, stream, local, evs, host, precision, steps, warmup):
     return leg, b, ids
 
 
+def batch_accuracy(evs, host, e_of, nsteps, stream, local):
+    """Error against FP64 of the smallest, the median and the largest event
+    of a batch after `nsteps` steps (e_of(i): the batch's e of event i)."""
+    order = sorted(range(len(evs)), key=lambda i: evs[i]["N"])
+    errs = {}
+    for i in sorted({order[0], order[len(order) // 2], order[-1]}):
+        ref, spread = fp64_reference_e(evs[i]["N"], host[i], nsteps, stream, local)
+        errs[f"event{i}_N{evs[i]['N']}"] = {"rel_l1_e": rel_l1(e_of(i), ref),
+                                            "fp64_ulp_flip_spread": spread}
+    return accuracy_summary(errs, nsteps)
+
+
 def batch_leg(ranks, stream, local, n_events=64, precision="mixed", steps=100, warmup=12):
     """Config 3 on the headline line: 64 uneven events (hot spots + radial
     flow, N from {48, 64, 96, 128, 160}) advanced as one batch, one launch
@@ -738,15 +750,8 @@ def batch_leg(ranks, stream, local, n_events=64, precision="mixed", steps=100, w
     host = [W.event_prims(ev).as_list() for ev in evs]
     leg, b, ids = _batch_timed(ranks, stream, local, evs, host, precision, steps, warmup)
     if ranks.rank == 0:
-        # error against FP64 of the smallest, the median and the largest event
-        order = sorted(range(len(evs)), key=lambda i: evs[i]["N"])
-        errs = {}
-        for i in sorted({order[0], order[len(order) // 2], order[-1]}):
-            e_b = b.get_primitives(ids[i])["e"]
-            ref, spread = fp64_reference_e(evs[i]["N"], host[i], warmup + steps, stream, local)
-            errs[f"event{i}_N{evs[i]['N']}"] = {"rel_l1_e": rel_l1(e_b, ref),
-                                                "fp64_ulp_flip_spread": spread}
-        leg["accuracy"] = accuracy_summary(errs, warmup + steps)
+        leg["accuracy"] = batch_accuracy(evs, host, lambda i: b.get_primitives(ids[i])["e"],
+                                         warmup + steps, stream, local)
     b.close()
     leg["workload"] = f"batch_{n_events}_events"
     leg["sizes"] = "N uniform in {48,64,96,128,160}, grids N^3, 5-40 hot spots, v_r = 0.1 r/R_box"
@@ -794,6 +799,8 @@ def run_batch(args):
            "step": "all events: add from pinned host (includes the autotuner), 100 steps, "
                    "primitives to pinned host"}
     b.close()
+    accuracy = batch_accuracy(evs, host, lambda i: outs[i][0], 100, stream, local) \
+        if rank == 0 else None
 
     # the same events one context at a time (each with its own launches)
     t_single = 0.0
@@ -825,6 +832,7 @@ def run_batch(args):
                       "items_per_step": leg["items_per_step"]},
             "one_context_per_event": {"value": single_rate, "unit": UNIT,
                                       "batch_speedup": leg["value"] / world / single_rate},
+            "accuracy": accuracy,
         }
         print(json.dumps(out), flush=True)
     ranks.close()
@@ -1008,8 +1016,10 @@ def timed_steps(solver, stream, k):
 
 def run_fixed(args):
     """tube64: the 64^3 planar shock tube, FP64 (and FP32 beside it), 40
-    steps; blast512: the 512^3 spherical blast, FP32 and MIXED for 500 steps
-    and FP64 timed over 10 steps, with the drift of the E and R totals."""
+    steps, each against the oracle run of the CPU baseline; blast512: the
+    512^3 spherical blast, FP32 and MIXED for 500 steps and FP64 timed over
+    10 steps, with the drift of the E and R totals."""
+    import numpy as np
     import torch
 
     from paper_1206_0919_gb300 import shasta as S
@@ -1032,6 +1042,7 @@ def run_fixed(args):
         legs = (("fp32", steps), ("mixed", steps), ("fp64", 10))
     ncell = N ** 3
     out = {}
+    finals = {}  # tube64: final conserved state of each leg
     for prec, k in legs:
         with S.Solver((N, N, N), precision=prec, stream=stream.cuda_stream, device=local) as s:
             s.set_primitives(*prims.as_list())
@@ -1043,6 +1054,8 @@ def run_fixed(args):
                          "ms_per_step": secs * 1e3 / k,
                          "drift_E": abs(t1[0] - t0[0]) / abs(t0[0]),
                          "drift_R": abs(t1[4] - t0[4]) / abs(t0[4]), "clamps": s.counters()}
+            if args.workload == "tube64":
+                finals[prec] = s.get_conserved()
     main_prec = legs[0][0]
     cpu = None
     if args.workload == "tube64" and not args.no_cpu_baseline:
@@ -1052,10 +1065,23 @@ def run_fixed(args):
         P = OR.params((N, N, N))
         U = O.prim2cons(P, *prims.as_list())
         t = time.perf_counter()
-        O.step(P, U, steps)
+        ref = O.step(P, U, steps)
         dt = time.perf_counter() - t
         cpu = {"value": ncell * steps / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"the whole workload ({steps} oracle steps, {dt:.1f} s)"}
+        # the legs' results against this oracle run: FP64 per cell (relative
+        # error, floored at 1e-14 of the field's largest value where it is
+        # zero), FP32 relative L1 per field
+        for prec, got in finals.items():
+            if prec == "fp64":
+                out[prec]["max_rel_err_per_cell_vs_oracle"] = max(
+                    float(np.max(np.abs(g - o) /
+                                 np.maximum(np.abs(o), max(1e-14 * np.abs(o).max(), 1e-300))))
+                    for g, o in zip(got, ref))
+            else:
+                out[prec]["rel_l1_vs_oracle"] = max(
+                    float(np.abs(g - o).sum() / max(np.abs(o).sum(), 1e-300))
+                    for g, o in zip(got, ref))
     if rank == 0:
         word = 8 if main_prec == "fp64" else 4
         line = {"metric": METRIC, "value": out[main_prec]["value"], "unit": UNIT, "n_gpus": 1,
