@@ -1057,6 +1057,25 @@ def run_fixed(args):
             if args.workload == "tube64":
                 finals[prec] = s.get_conserved()
     main_prec = legs[0][0]
+    if args.workload != "tube64":
+        # accuracy of the same setup at 128^3 (radius 10 cells, 125 steps):
+        # each single-precision leg against the FP64 path from the same
+        # float32-rounded state, beside the stored single-precision yardstick
+        n, k = 128, 125
+        small = W.blast(N=n, radius=10.0).as_list()
+        ref, spread = fp64_reference_e(n, small, k, stream, local)
+        with open(os.path.join(ROOT, "tests", "golden", "sensitivity.json")) as f:
+            yard = json.load(f)["blast_128"]["single_precision"]["max"][str(k)]
+        for prec in ("fp32", "mixed"):
+            with S.Solver((n, n, n), precision=prec, delta=1e-6, stream=stream.cuda_stream,
+                          device=local) as s:
+                s.set_primitives(*small)
+                s.step(k)
+                err = rel_l1(s.get_primitives()["e"], ref)
+            out[prec]["accuracy_128"] = {"rel_l1_e": err, "steps": k,
+                                         "single_precision_yardstick": yard,
+                                         "ratio_to_yardstick": err / yard,
+                                         "fp64_ulp_flip_spread": spread}
     cpu = None
     if args.workload == "tube64" and not args.no_cpu_baseline:
         from oracle import oracle as OR
