@@ -257,8 +257,10 @@ def job_rate(world, units_per_rank, seconds):
 
 # ---------------------------------------------------------- CPU oracle ----
 
-def oracle_rate(N, max_steps=3, target_s=10.0, threads=None):
-    """Oracle (FP64 C reference) cell-updates/s on the host cores."""
+def oracle_rate(N, max_steps=EVENT_STEPS, target_s=10.0, threads=None):
+    """Oracle (FP64 C reference) cell-updates/s on the host cores: whole
+    steps of the workload's state until about target_s seconds of work (a
+    bounded sample of the event's max_steps steps)."""
     from oracle import oracle as OR
     O = OR.default()
     threads = threads or (os.cpu_count() or 1)
