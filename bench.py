@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "mixed", "mixed_fp64", "fp64"], default="fp32")
     ap.add_argument("--grid", type=int, default=N_GRID)
-    ap.add_argument("--e2e-events", type=int, default=4)
+    ap.add_argument("--e2e-events", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--no-legs", action="store_true",
