@@ -72,6 +72,39 @@ def test_bad_scheme_is_rejected_before_any_device_call(lib):
         assert ei.value.status == S.EINVAL, kw
 
 
+@pytest.mark.parametrize("shape,kw,needle", [
+    ((0, 4, 4), {}, "grid sizes"),
+    ((4, -1, 4), {}, "grid sizes"),
+    ((1 << 16, 1 << 16, 1), {"precision": "fp64"}, "plane too large"),
+    ((1, 1 << 16, 1 << 16), {"precision": "fp64"}, "plane too large"),
+    ((2048, 2048, 1024), {}, "2^32 cells"),
+    ((2048, 2048, 1024), {"precision": "mixed"}, "2^32 cells"),
+    ((4, 4, 4), {"lam": 0.0}, "lambda"),
+    ((4, 4, 4), {"lam": 0.51}, "lambda"),
+    ((4, 4, 4), {"lam": float("nan")}, "lambda"),
+    ((4, 4, 4), {"dx": 0.0}, "dx"),
+    ((4, 4, 4), {"dx": float("inf")}, "dx"),
+    ((4, 4, 4), {"eta": -0.1}, "eta"),
+    ((4, 4, 4), {"eta": 0.6}, "eta"),
+    ((4, 4, 4), {"delta": 0.5}, "delta"),
+    ((4, 4, 4), {"delta": -1e-3}, "delta"),
+    ((4, 4, 4), {"bc": 9}, "boundary"),
+    ((4, 4, 4), {"eos": 7}, "EoS"),
+    ((4, 4, 4), {"eos": "bag", "bag_B": 0.2, "bag_ec": 0.5}, "4B <= e_c"),
+    ((4, 4, 4), {"eos": "bag", "bag_B": -0.1}, "4B <= e_c"),
+])
+def test_bad_grids_and_options_are_rejected_before_any_device_call(lib, shape, kw, needle):
+    """Grid sizes (each >= 1; every plane < 2^31 lines; FP32 / MIXED grids
+    under 2^32 cells, the kernels' 32-bit cell offsets), the time-step ratio
+    (0 < lambda <= 0.5), dx, eta, the clamp margin, the boundary rule and
+    the EoS parameters are checked on the host first: EINVAL with the
+    reason, on any machine, before the library looks for a device."""
+    with pytest.raises(S.ShastaError) as ei:
+        S.Solver(shape, **kw)
+    assert ei.value.status == S.EINVAL, (shape, kw)
+    assert needle in str(ei.value), str(ei.value)
+
+
 def test_bad_eos_tables_are_rejected(lib):
     """A tabulated EoS must be finite, p >= 0, monotone and causal
     (0 <= dp/de < 1), with at least two values and table_de > 0; MIXED has
