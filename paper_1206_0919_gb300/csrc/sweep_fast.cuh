@@ -367,7 +367,22 @@ __device__ __forceinline__ unsigned rec32(float E, float mx, float my, float mz,
   if constexpr (REC == REC_F64 && EOS != EOS_TABLE)
     return rec64<EOS>(E, mx, my, mz, m1, omd64, B, ec, w, p);
   unsigned clamped = 0;
-  float M2 = fmaf(mx, mx, fmaf(my, my, mz * mz));
+  float M2, M2lo = 0.0f;  // |M|^2; REC_DF: an unevaluated sum M2 + M2lo
+  if constexpr (REC == REC_DF) {
+    // |M|^2 = hi + lo from error-free products and compensated sums
+    const float a = mx * mx, a_l = fmaf(mx, mx, -a);
+    const float b = my * my, b_l = fmaf(my, my, -b);
+    const float c = mz * mz, c_l = fmaf(mz, mz, -c);
+    const float s1 = a + b;
+    float bb = s1 - a;
+    const float r1 = (a - (s1 - bb)) + (b - bb);
+    M2 = s1 + c;
+    bb = M2 - s1;
+    const float r2 = (s1 - (M2 - bb)) + (c - bb);
+    M2lo = ((a_l + b_l) + c_l) + (r1 + r2);
+  } else {
+    M2 = fmaf(mx, mx, fmaf(my, my, mz * mz));
+  }
   const float E2 = E * E;
   const float lim = omd * E;
   const float L2 = lim * lim;
@@ -380,20 +395,9 @@ __device__ __forceinline__ unsigned rec32(float E, float mx, float my, float mz,
     D = E2 - M2;
     clamped = 1;
   } else if (REC == REC_DF) {
-    // D = E^2 - |M|^2 with |M|^2 = hi + lo from error-free products and
-    // compensated sums; E^2 - hi in one fused multiply-add (one rounding of
+    // D = E^2 - |M|^2: E^2 - hi in one fused multiply-add (one rounding of
     // the exact difference), then lo
-    const float a = mx * mx, a_l = fmaf(mx, mx, -a);
-    const float b = my * my, b_l = fmaf(my, my, -b);
-    const float c = mz * mz, c_l = fmaf(mz, mz, -c);
-    const float s1 = a + b;
-    float bb = s1 - a;
-    const float r1 = (a - (s1 - bb)) + (b - bb);
-    const float hi = s1 + c;
-    bb = hi - s1;
-    const float r2 = (s1 - (hi - bb)) + (c - bb);
-    const float lo = ((a_l + b_l) + c_l) + (r1 + r2);
-    D = fmaf(E, E, -hi) - lo;
+    D = fmaf(E, E, -M2) - M2lo;
   } else {
     D = E2 - M2;
   }
