@@ -192,8 +192,11 @@ shasta_status shasta_sweep(shasta_ctx* ctx, int axis);
 /* Times the launch choices of the sweep kernels for this grid and keeps the
  * fastest per axis.  FP32 / MIXED: work range length and register variant (a
  * sweep's positions, line groups of 32 lines x positions along the axis, are
- * cut into equal ranges handed to the resident warps).  FP64: the length of
- * the line segments streamed one per thread.  No choice changes results.
+ * cut into as many ranges as that length gives, handed to the resident warps;
+ * the cuts balance each range's streaming cost, its cells plus a 13-position
+ * halo per line it touches, unless the environment sets SHASTA_BALANCE=0).
+ * FP64: the length of the line segments streamed one per thread.  No choice
+ * changes results.
  * Runs sweeps from the current state into the spare buffer only, so the
  * state is unchanged; synchronous.  Errors: EINVAL (state not set), ECUDA. */
 shasta_status shasta_autotune(shasta_ctx* ctx);

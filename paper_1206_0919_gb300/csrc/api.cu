@@ -6,6 +6,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -63,6 +64,13 @@ struct shasta_ctx {
   bool tuned = false;     // autotuned launch choice below is valid
   int tune_var[3] = {0, 0, 0};
   long long tune_range[3] = {0, 0, 0};
+  // FP32 / MIXED: per axis, the bounds of balanced work ranges (device), built
+  // for one range length; off with SHASTA_BALANCE=0 or a forced range length
+  bool balance = true;
+  int* d_ranges[3] = {};
+  long long ranges_cap[3] = {};  // capacity in bounds
+  long long ranges_len[3] = {};  // range length the table was built for (0: none)
+  long long ranges_n[3] = {};    // ranges in the table
   cudaGraphExec_t graph = nullptr;  // six steps from phase 0, buffer 0
   std::string err;
 };
@@ -182,6 +190,83 @@ long long range_for(long long total, long long warps, double share) {
   return len < 24 ? 24 : len;
 }
 
+void drop_graph(shasta_ctx* c);
+
+// Bounds of at most R contiguous work ranges over `total` positions (lines
+// of n positions, one after the other) with about equal streaming cost: a
+// range costs the positions of its pieces (its parts within one line) plus
+// `halo` positions of lead-in and lag per piece, so a range that crosses a
+// line end is shorter.  Bounds inside a line fall on multiples of `align`;
+// a range takes no further piece shorter than 8 positions.  The smallest
+// cost bound T that needs at most R ranges is found by bisection.
+std::vector<int> balanced_bounds(long long total, long long n, long long R, long long align,
+                                 long long halo) {
+  const long long kMinPiece = 8;
+  auto cut = [&](long long T, std::vector<int>* out) -> long long {
+    long long x = 0, count = 0;
+    if (out) out->assign(1, 0);
+    while (x < total) {
+      long long budget = T, y = x;
+      while (y < total && budget > halo) {
+        const long long line_end = (y / n + 1) * n;
+        long long take = std::min(line_end - y, budget - halo);
+        if (y + take < line_end) {
+          const long long e = y + take;
+          take -= (e - (e / n) * n) % align;  // end on a chunk boundary of the line
+        }
+        if (take <= 0 || (y != x && take < kMinPiece && y + take < line_end)) break;
+        y += take;
+        budget -= take + halo;
+      }
+      if (y == x) y = std::min((x / n + 1) * n, x + align);  // at least one chunk
+      ++count;
+      x = y;
+      if (out) out->push_back((int)y);
+    }
+    return count;
+  };
+  long long lo = halo + 1, hi = total + halo * (total / n + 2) + 1;
+  while (lo < hi) {
+    const long long mid = lo + (hi - lo) / 2;
+    if (cut(mid, nullptr) <= R)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  std::vector<int> b;
+  cut(lo, &b);
+  return b;
+}
+
+// Makes the device table of balanced ranges of an axis match range length
+// `len` (as many ranges as uniform ranges of len would give); synchronous,
+// so never called while a graph is being captured.
+shasta_status ensure_ranges(shasta_ctx* c, int axis, long long len) {
+  if (c->o.precision == SHASTA_FP64 || !c->balance || c->force_range > 0 || len < 1) return SHASTA_OK;
+  if (c->ranges_len[axis] == len) return SHASTA_OK;
+  const long long n = axis == 0 ? c->g.nx : (axis == 1 ? c->g.ny : c->g.nz);
+  const long long total = work_positions(c, axis);
+  const long long R = (total + len - 1) / len;
+  const std::vector<int> b = balanced_bounds(total, n, R, axis == 0 ? 8 : 1, 13);
+  drop_graph(c);  // a captured graph holds the old table and its size
+  c->ranges_len[axis] = 0;
+  if ((long long)b.size() > c->ranges_cap[axis]) {
+    CK(cudaStreamSynchronize(c->stream), "ranges");  // no launch still reads the old table
+    cudaFree(c->d_ranges[axis]);
+    c->d_ranges[axis] = nullptr;
+    c->ranges_cap[axis] = 0;
+    CK(cudaMalloc(&c->d_ranges[axis], b.size() * sizeof(int)), "cudaMalloc ranges");
+    c->ranges_cap[axis] = (long long)b.size();
+  }
+  CK(cudaMemcpyAsync(c->d_ranges[axis], b.data(), b.size() * sizeof(int), cudaMemcpyHostToDevice,
+                     c->stream),
+     "upload ranges");
+  CK(cudaStreamSynchronize(c->stream), "upload ranges");
+  c->ranges_len[axis] = len;
+  c->ranges_n[axis] = (long long)b.size() - 1;
+  return SHASTA_OK;
+}
+
 SweepParams sweep_params(shasta_ctx* c, int axis, int from, int variant, long long range) {
   SweepParams P;
   memset(&P, 0, sizeof P);
@@ -235,9 +320,14 @@ SweepParams sweep_params(shasta_ctx* c, int axis, int from, int variant, long lo
   P.range_len = range < 1 ? 1 : range;  // FP64: cells per line segment
   P.variant = variant;
   if (c->o.precision != SHASTA_FP64) {
+    // the balanced table built for this range length, if any
+    if (c->balance && c->force_range == 0 && c->ranges_len[axis] == P.range_len) {
+      P.ranges = c->d_ranges[axis];
+      P.nranges = c->ranges_n[axis];
+    }
     // at most one wave of resident warps loops over the ranges
     const long long total = work_positions(c, axis);
-    const long long ranges = (total + P.range_len - 1) / P.range_len;
+    const long long ranges = P.ranges ? P.nranges : (total + P.range_len - 1) / P.range_len;
     long long blocks = (ranges + c->wpb - 1) / c->wpb;
     const int wpsm = c->occ[c->eos.kind][axis][variant];
     const long long wave = (long long)c->sm_count * (wpsm > 0 ? wpsm / c->wpb : 1);
@@ -274,6 +364,19 @@ void launch_choice(const shasta_ctx* c, int axis, int& variant, long long& range
   const long long warps = (long long)c->sm_count * c->occ[c->eos.kind][axis][variant];
   range = c->tuned ? c->tune_range[axis] : range_for(work_positions(c, axis), warps, 1.0);
   if (c->force_range > 0) range = c->force_range;
+}
+
+// Balanced range tables for the current launch choice of every axis (before
+// launches or a capture).
+shasta_status prepare_ranges(shasta_ctx* c) {
+  for (int axis = 0; axis < 3; ++axis) {
+    int v;
+    long long r;
+    launch_choice(c, axis, v, r);
+    const shasta_status st = ensure_ranges(c, axis, r);
+    if (st != SHASTA_OK) return st;
+  }
+  return SHASTA_OK;
 }
 
 cudaError_t launch_params(shasta_ctx* c, int axis, const SweepParams& P) {
@@ -382,6 +485,8 @@ shasta_status autotune(shasta_ctx* c) {
         }
       }
       for (int ci = 0; ci < nc && st == SHASTA_OK; ++ci) {
+        st = ensure_ranges(c, axis, cands[ci]);
+        if (st != SHASTA_OK) break;
         float ms = 0;
         const cudaError_t ce = time_choice(c, axis, sweep_params(c, axis, c->cur, var, cands[ci]),
                                            f64 ? 1 : 2, f64 ? 2 : 4, e0, e1, ms);
@@ -398,6 +503,7 @@ shasta_status autotune(shasta_ctx* c) {
     }
     c->tune_var[axis] = bv;
     c->tune_range[axis] = br;
+    if (st == SHASTA_OK) st = ensure_ranges(c, axis, br);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -419,6 +525,7 @@ void release(shasta_ctx* c) {
   cudaFree(c->partials);
   cudaFree(c->d_tot);
   cudaFree(c->d_count);
+  for (int a = 0; a < 3; ++a) cudaFree(c->d_ranges[a]);
   cudaFreeHost(c->h_small);
   drop_graph(c);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -541,6 +648,8 @@ shasta_status shasta_create(const shasta_grid* g, double dx, double lambda, cons
       c->sm_count = sms;
     const char* v = getenv("SHASTA_RANGE");
     if (v && atoll(v) > 0) c->force_range = atoll(v);
+    v = getenv("SHASTA_BALANCE");
+    if (v && atoi(v) == 0) c->balance = false;
     v = getenv("SHASTA_VARIANT");
     if (v && atoi(v) >= 0 && atoi(v) <= 1) c->force_variant = atoi(v);
   }
@@ -694,6 +803,10 @@ shasta_status shasta_step(shasta_ctx* c, int nsteps) {
     shasta_status st = autotune(c);
     if (st != SHASTA_OK) return st;
   }
+  if (nsteps > 0) {
+    const shasta_status st = prepare_ranges(c);
+    if (st != SHASTA_OK) return st;
+  }
   while (nsteps > 0) {
     if (c->o.use_graphs && nsteps >= 6 && c->steps % 6 == 0 && c->cur == 0) {
       // six steps (18 sweeps) bring phase and buffer back: one graph
@@ -751,6 +864,8 @@ shasta_status shasta_sweep(shasta_ctx* c, int axis) {
   if (axis < 0 || axis > 2) return fail(c, SHASTA_EINVAL, "axis must be 0, 1 or 2");
   if (!c->state_set) return fail(c, SHASTA_EINVAL, "state not set");
   DeviceGuard dg(c->device);
+  const shasta_status st = prepare_ranges(c);
+  if (st != SHASTA_OK) return st;
   CK(launch_sweep(c, axis), "sweep launch");
   return SHASTA_OK;
 }

@@ -72,6 +72,8 @@ struct SweepParams {
   unsigned long long* clamp_count;  // cells recovered with |M| clamped or E <= 0
   long long range_len;              // fast kernels: positions per work range (>= 1; batches: 0
                                     // = whole line groups, BatchList.prefix then counts groups)
+  const int* ranges;                // one event, when set: range r is positions
+  long long nranges;                // [ranges[r], ranges[r+1]), r < nranges (balanced cuts)
   int variant;                      // fast kernels: launch variant (0: capped registers, 1: not)
   long long blocks;                 // fast kernels: grid size (one wave of resident warps)
   // fast kernels: state as (E, Mx, My, Mz) quads per cell plus an R array

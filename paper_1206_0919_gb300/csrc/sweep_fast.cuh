@@ -926,7 +926,9 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, i
 // takes ranges w, w + warps, ...  A range is streamed piece by piece (one
 // piece per line group it touches, each with its own halo); on the x path
 // range boundaries are moved down to 8-cell chunk boundaries of their line.
-// A batch may instead take whole line groups as work units (range_len 0).
+// One event may instead take the host's table of range bounds (P.ranges:
+// ranges of equal streaming cost, chunk-aligned on the x path); a batch may
+// take whole line groups as work units (range_len 0).
 template <int EOS, int AXIS, int REC, int WARPS, int RING, int DIST, bool BATCH, bool AF = true>
 __device__ __forceinline__ void sweep_items(const SweepParams& P, const BatchList& L) {
   constexpr bool XP = AXIS == 0;
@@ -997,11 +999,18 @@ __device__ __forceinline__ void sweep_items(const SweepParams& P, const BatchLis
     const int n = P.n;
     const int total = (int)((P.plane + LANES - 1) / LANES) * n;
     auto bound = [&](int x) -> int { return XP && x < total ? x - (x % n) % CH : x; };
-    const int nranges = (total + len - 1) / len;
+    // uniform ranges of len positions, or the host's table of balanced bounds
+    const int nranges = P.ranges ? (int)P.nranges : (total + len - 1) / len;
 #pragma unroll 1
     for (int r = first; r < nranges; r += nwarps) {
-      int x = bound(r * len);
-      const int end = bound(min(r * len + len, total));
+      int x, end;
+      if (P.ranges) {
+        x = P.ranges[r];
+        end = P.ranges[r + 1];
+      } else {
+        x = bound(r * len);
+        end = bound(min(r * len + len, total));
+      }
 #pragma unroll 1
       while (x < end) {
         const int g = x / n;

@@ -275,9 +275,9 @@ def test_clamp_counter():
 
 @pytest.mark.parametrize("precision", ["fp32", "mixed", "mixed_fp64", "fp64"])
 def test_graphs_and_launch_choices_bitwise(monkeypatch, precision):
-    """CUDA-graph replay, the autotuner and every forced launch choice (work
-    range length, register variant; FP64: line segment length) give bitwise
-    identical states."""
+    """CUDA-graph replay, the autotuner, balanced and uniform work ranges and
+    every forced launch choice (work range length, register variant; FP64:
+    line segment length) give bitwise identical states."""
     shape = (72, 56, 48)
     pr = W.hot_spots(shape=shape, seed=21, n_spots=6, sigma=(2.0, 4.0), radial_flow=0.1)
     O = oracle()
@@ -291,6 +291,11 @@ def test_graphs_and_launch_choices_bitwise(monkeypatch, precision):
 
     ref = run(autotune=False, use_graphs=False)
     outs = [run(autotune=True, use_graphs=True)]
+    # uniform instead of balanced work ranges (FP32 / MIXED)
+    monkeypatch.setenv("SHASTA_BALANCE", "0")
+    outs.append(run(autotune=False, use_graphs=True))
+    outs.append(run(autotune=True, use_graphs=False))
+    monkeypatch.delenv("SHASTA_BALANCE")
     # forced work ranges (FP64: segment lengths, whole lines for 100000)
     for rng, var in ((100000, 0), (37, 1), (24, 0), (5, 1)):
         monkeypatch.setenv("SHASTA_RANGE", str(rng))
