@@ -432,7 +432,10 @@ def run_ours(args):
 
     # end-to-end: events through the public API with pinned host buffers.
     # Two contexts on two streams take the events in turn, so one event's
-    # copies in and out (and the input check) overlap the other's steps.
+    # copies in and out (and the input check) overlap the other's steps; an
+    # event's steps wait (on the device) for the previous event's steps, so
+    # the two never share the GPU and the older event finishes first, while
+    # the newer one runs.
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
     host_in = [pin(a) for a in prims.as_list()]
     stream2 = torch.cuda.Stream()
@@ -445,13 +448,19 @@ def run_ours(args):
         c.set_primitives(*host_in)
         c.step(6)
         c.get_primitives(o)
+    streams = (stream, stream2)
     ranks.barrier()
     t0 = time.perf_counter()
     prev = None
+    steps_done = [None, None]
     for k in range(args.e2e_events):
         cur = k % 2
         ctxs[cur].set_primitives(*host_in)
+        if prev is not None:
+            streams[cur].wait_event(steps_done[prev])
         ctxs[cur].step(EVENT_STEPS)
+        steps_done[cur] = torch.cuda.Event()
+        steps_done[cur].record(streams[cur])
         if prev is not None:
             ctxs[prev].get_primitives(outs[prev])
         prev = cur
@@ -461,7 +470,8 @@ def run_ours(args):
            "h2d_bytes_per_step": 5 * 8 * ncell, "d2h_bytes_per_step": 6 * 8 * ncell,
            "step": f"one event: set_primitives from pinned host, {EVENT_STEPS} steps, "
                    "get_primitives to pinned host; two contexts on two streams take the "
-                   "events in turn (one event's copies overlap the other's steps)",
+                   "events in turn (one event's copies overlap the other's steps, which "
+                   "start on the device when the previous event's steps end)",
            "events": args.e2e_events}
     solver2.close()
     solver.close()

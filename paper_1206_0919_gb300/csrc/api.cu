@@ -25,6 +25,18 @@ const char* kVersion = "shasta-gb300 0.1 (sm_103a)";
 // Fixed permutation of the sweep axes, Sec. 3.1.4.
 const int kAxisTable[18] = {0, 1, 2, 0, 2, 1, 2, 0, 1, 2, 1, 0, 1, 2, 0, 1, 0, 2};
 
+// Work-range cost model of the FP32 / MIXED sweeps (measured per warp on
+// 200^3 and 256^3 hot spots): a piece costs its positions plus 13 of lead-in
+// and lag, plus about 11 for each line end it touches (ghost positions); the
+// three CTAs resident on an SM, in launch order, ran 8% faster / on par / 9%
+// slower than the mean with equal shares.
+constexpr double kEdgeCost = 11.0;
+constexpr double kRankSkew = 0.04;
+// Rank skews the autotuner times (with equal shares, the last CTA of an SM
+// finished up to 9% after the mean; measured optimum 0.04-0.08 for one range
+// per warp: 0.8-1.3% off the 200^3 / 256^3 step, larger skews slower).
+const double kSkewCands[] = {0.0, 0.04, 0.08};
+
 }  // namespace
 
 struct shasta_ctx {
@@ -70,7 +82,15 @@ struct shasta_ctx {
   int* d_ranges[3] = {};
   long long ranges_cap[3] = {};  // capacity in bounds
   long long ranges_len[3] = {};  // range length the table was built for (0: none)
+  int ranges_var[3] = {};        // launch variant the table was built for
   long long ranges_n[3] = {};    // ranges in the table
+  // work shares of the CTAs resident on one SM, by launch order: the first
+  // CTA takes 1 + skew times the mean work, the last 1 - skew (the warp
+  // schedulers favour older CTAs, so equal shares finish staggered)
+  double rank_skew[3] = {kRankSkew, kRankSkew, kRankSkew};  // per axis
+  bool force_skew = false;  // rank skew set by the environment (not tuned)
+  double ranges_skew[3] = {};  // rank skew the table was built for
+  double edge_cost = kEdgeCost;  // streaming cost of a line end a piece touches, in positions
   cudaGraphExec_t graph = nullptr;  // six steps from phase 0, buffer 0
   std::string err;
 };
@@ -193,30 +213,39 @@ long long range_for(long long total, long long warps, double share) {
 void drop_graph(shasta_ctx* c);
 
 // Bounds of at most R contiguous work ranges over `total` positions (lines
-// of n positions, one after the other) with about equal streaming cost: a
-// range costs the positions of its pieces (its parts within one line) plus
-// `halo` positions of lead-in and lag per piece, so a range that crosses a
-// line end is shorter.  Bounds inside a line fall on multiples of `align`;
-// a range takes no further piece shorter than 8 positions.  The smallest
-// cost bound T that needs at most R ranges is found by bisection.
+// of n positions, one after the other) with streaming costs in proportion to
+// weight(r): a piece (the part of a range within one line) costs its
+// positions plus `halo` positions of lead-in and lag plus `edge` for each
+// line end it touches, so a range that crosses or reaches a line end is
+// shorter.  Bounds inside a line fall on multiples of `align`; a range takes
+// no further piece shorter than 8 positions.  The smallest cost scale T that
+// needs at most R ranges is found by bisection.
+template <class Weight>
 std::vector<int> balanced_bounds(long long total, long long n, long long R, long long align,
-                                 long long halo) {
+                                 double halo, double edge, Weight weight) {
   const long long kMinPiece = 8;
-  auto cut = [&](long long T, std::vector<int>* out) -> long long {
+  auto cut = [&](double T, std::vector<int>* out) -> long long {
     long long x = 0, count = 0;
     if (out) out->assign(1, 0);
     while (x < total) {
-      long long budget = T, y = x;
-      while (y < total && budget > halo) {
+      double budget = T * weight(count);
+      long long y = x;
+      while (y < total) {
         const long long line_end = (y / n + 1) * n;
-        long long take = std::min(line_end - y, budget - halo);
-        if (y + take < line_end) {
+        const double fixed = halo + (y == line_end - n ? edge : 0.0);
+        if (budget <= fixed) break;
+        long long take;
+        if ((double)(line_end - y) + fixed + edge <= budget) {
+          take = line_end - y;  // the rest of the line, its end included
+        } else {
+          take = std::min(line_end - y - 1, (long long)(budget - fixed));
           const long long e = y + take;
           take -= (e - (e / n) * n) % align;  // end on a chunk boundary of the line
+          if (line_end - (y + take) < kMinPiece) take = line_end - y;  // no sliver left over
         }
         if (take <= 0 || (y != x && take < kMinPiece && y + take < line_end)) break;
+        budget -= (double)take + fixed + (y + take == line_end ? edge : 0.0);
         y += take;
-        budget -= take + halo;
       }
       if (y == x) y = std::min((x / n + 1) * n, x + align);  // at least one chunk
       ++count;
@@ -225,29 +254,42 @@ std::vector<int> balanced_bounds(long long total, long long n, long long R, long
     }
     return count;
   };
-  long long lo = halo + 1, hi = total + halo * (total / n + 2) + 1;
-  while (lo < hi) {
-    const long long mid = lo + (hi - lo) / 2;
+  double lo = 0.0, hi = 2.0 * ((double)total + (halo + 2.0 * edge) * (double)(total / n + 2)) + 1.0;
+  for (int it = 0; it < 64 && hi - lo > 1e-3; ++it) {
+    const double mid = 0.5 * (lo + hi);
     if (cut(mid, nullptr) <= R)
       hi = mid;
     else
-      lo = mid + 1;
+      lo = mid;
   }
   std::vector<int> b;
-  cut(lo, &b);
+  cut(hi, &b);
   return b;
 }
 
 // Makes the device table of balanced ranges of an axis match range length
 // `len` (as many ranges as uniform ranges of len would give); synchronous,
 // so never called while a graph is being captured.
-shasta_status ensure_ranges(shasta_ctx* c, int axis, long long len) {
+shasta_status ensure_ranges(shasta_ctx* c, int axis, long long len, int variant) {
   if (c->o.precision == SHASTA_FP64 || !c->balance || c->force_range > 0 || len < 1) return SHASTA_OK;
-  if (c->ranges_len[axis] == len) return SHASTA_OK;
+  if (c->ranges_len[axis] == len && c->ranges_var[axis] == variant &&
+      c->ranges_skew[axis] == c->rank_skew[axis])
+    return SHASTA_OK;
   const long long n = axis == 0 ? c->g.nx : (axis == 1 ? c->g.ny : c->g.nz);
   const long long total = work_positions(c, axis);
   const long long R = (total + len - 1) / len;
-  const std::vector<int> b = balanced_bounds(total, n, R, axis == 0 ? 8 : 1, 13);
+  // range r runs on warp r mod W of the launch (W = resident warps of one
+  // wave, blocks handed to the SMs in order), in the CTA of launch rank
+  // (r mod W) / wpb / SMs on its SM
+  const int wpsm = c->occ[c->eos.kind][axis][variant];
+  const long long K = wpsm > 0 ? wpsm / c->wpb : 1;  // CTAs per SM
+  const long long W = (long long)c->sm_count * K * c->wpb;
+  const double skew = K > 1 ? c->rank_skew[axis] : 0.0;
+  auto weight = [&](long long r) {
+    const long long rank = (r % W) / c->wpb / c->sm_count;
+    return 1.0 + skew * (1.0 - 2.0 * (double)rank / (double)(K - 1 > 0 ? K - 1 : 1));
+  };
+  const std::vector<int> b = balanced_bounds(total, n, R, axis == 0 ? 8 : 1, 13.0, c->edge_cost, weight);
   drop_graph(c);  // a captured graph holds the old table and its size
   c->ranges_len[axis] = 0;
   if ((long long)b.size() > c->ranges_cap[axis]) {
@@ -263,6 +305,8 @@ shasta_status ensure_ranges(shasta_ctx* c, int axis, long long len) {
      "upload ranges");
   CK(cudaStreamSynchronize(c->stream), "upload ranges");
   c->ranges_len[axis] = len;
+  c->ranges_var[axis] = variant;
+  c->ranges_skew[axis] = c->rank_skew[axis];
   c->ranges_n[axis] = (long long)b.size() - 1;
   return SHASTA_OK;
 }
@@ -321,7 +365,8 @@ SweepParams sweep_params(shasta_ctx* c, int axis, int from, int variant, long lo
   P.variant = variant;
   if (c->o.precision != SHASTA_FP64) {
     // the balanced table built for this range length, if any
-    if (c->balance && c->force_range == 0 && c->ranges_len[axis] == P.range_len) {
+    if (c->balance && c->force_range == 0 && c->ranges_len[axis] == P.range_len &&
+        c->ranges_var[axis] == variant && c->ranges_skew[axis] == c->rank_skew[axis]) {
       P.ranges = c->d_ranges[axis];
       P.nranges = c->ranges_n[axis];
     }
@@ -373,7 +418,7 @@ shasta_status prepare_ranges(shasta_ctx* c) {
     int v;
     long long r;
     launch_choice(c, axis, v, r);
-    const shasta_status st = ensure_ranges(c, axis, r);
+    const shasta_status st = ensure_ranges(c, axis, r, v);
     if (st != SHASTA_OK) return st;
   }
   return SHASTA_OK;
@@ -485,7 +530,7 @@ shasta_status autotune(shasta_ctx* c) {
         }
       }
       for (int ci = 0; ci < nc && st == SHASTA_OK; ++ci) {
-        st = ensure_ranges(c, axis, cands[ci]);
+        st = ensure_ranges(c, axis, cands[ci], var);
         if (st != SHASTA_OK) break;
         float ms = 0;
         const cudaError_t ce = time_choice(c, axis, sweep_params(c, axis, c->cur, var, cands[ci]),
@@ -503,7 +548,29 @@ shasta_status autotune(shasta_ctx* c) {
     }
     c->tune_var[axis] = bv;
     c->tune_range[axis] = br;
-    if (st == SHASTA_OK) st = ensure_ranges(c, axis, br);
+    // FP32 / MIXED: the work shares of the CTAs of an SM for that choice
+    if (!f64 && st == SHASTA_OK && c->balance && c->force_range == 0 && !c->force_skew) {
+      const double keep = c->rank_skew[axis];
+      double bs = keep;
+      float bms = 1e30f;
+      for (double sk : kSkewCands) {
+        c->rank_skew[axis] = sk;
+        st = ensure_ranges(c, axis, br, bv);
+        if (st != SHASTA_OK) break;
+        float ms = 0;
+        const cudaError_t ce = time_choice(c, axis, sweep_params(c, axis, c->cur, bv, br), 2, 4, e0, e1, ms);
+        if (ce != cudaSuccess) {
+          st = cuda_fail(c, ce, "autotune");
+          break;
+        }
+        if (ms < bms) {
+          bms = ms;
+          bs = sk;
+        }
+      }
+      c->rank_skew[axis] = st == SHASTA_OK ? bs : keep;
+    }
+    if (st == SHASTA_OK) st = ensure_ranges(c, axis, br, bv);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -652,6 +719,13 @@ shasta_status shasta_create(const shasta_grid* g, double dx, double lambda, cons
     if (v && atoi(v) == 0) c->balance = false;
     v = getenv("SHASTA_VARIANT");
     if (v && atoi(v) >= 0 && atoi(v) <= 1) c->force_variant = atoi(v);
+    v = getenv("SHASTA_RANK_SKEW");
+    if (v && atof(v) >= 0.0 && atof(v) < 0.5) {
+      c->rank_skew[0] = c->rank_skew[1] = c->rank_skew[2] = atof(v);
+      c->force_skew = true;
+    }
+    v = getenv("SHASTA_EDGE_COST");
+    if (v && atof(v) >= 0.0 && atof(v) <= 64.0) c->edge_cost = atof(v);
   }
   auto bail = [&](cudaError_t err, const char* where) {
     std::string m = std::string(where) + ": " + cudaGetErrorString(err);
