@@ -13,6 +13,7 @@
 
 #include "../../include/shasta.h"
 #include "kernels.h"
+#include "work_ranges.h"
 
 using namespace shasta;
 
@@ -212,61 +213,6 @@ long long range_for(long long total, long long warps, double share) {
 
 void drop_graph(shasta_ctx* c);
 
-// Bounds of at most R contiguous work ranges over `total` positions (lines
-// of n positions, one after the other) with streaming costs in proportion to
-// weight(r): a piece (the part of a range within one line) costs its
-// positions plus `halo` positions of lead-in and lag plus `edge` for each
-// line end it touches, so a range that crosses or reaches a line end is
-// shorter.  Bounds inside a line fall on multiples of `align`; a range takes
-// no further piece shorter than 8 positions.  The smallest cost scale T that
-// needs at most R ranges is found by bisection.
-template <class Weight>
-std::vector<int> balanced_bounds(long long total, long long n, long long R, long long align,
-                                 double halo, double edge, Weight weight) {
-  const long long kMinPiece = 8;
-  auto cut = [&](double T, std::vector<int>* out) -> long long {
-    long long x = 0, count = 0;
-    if (out) out->assign(1, 0);
-    while (x < total) {
-      double budget = T * weight(count);
-      long long y = x;
-      while (y < total) {
-        const long long line_end = (y / n + 1) * n;
-        const double fixed = halo + (y == line_end - n ? edge : 0.0);
-        if (budget <= fixed) break;
-        long long take;
-        if ((double)(line_end - y) + fixed + edge <= budget) {
-          take = line_end - y;  // the rest of the line, its end included
-        } else {
-          take = std::min(line_end - y - 1, (long long)(budget - fixed));
-          const long long e = y + take;
-          take -= (e - (e / n) * n) % align;  // end on a chunk boundary of the line
-          if (line_end - (y + take) < kMinPiece) take = line_end - y;  // no sliver left over
-        }
-        if (take <= 0 || (y != x && take < kMinPiece && y + take < line_end)) break;
-        budget -= (double)take + fixed + (y + take == line_end ? edge : 0.0);
-        y += take;
-      }
-      if (y == x) y = std::min((x / n + 1) * n, x + align);  // at least one chunk
-      ++count;
-      x = y;
-      if (out) out->push_back((int)y);
-    }
-    return count;
-  };
-  double lo = 0.0, hi = 2.0 * ((double)total + (halo + 2.0 * edge) * (double)(total / n + 2)) + 1.0;
-  for (int it = 0; it < 64 && hi - lo > 1e-3; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (cut(mid, nullptr) <= R)
-      hi = mid;
-    else
-      lo = mid;
-  }
-  std::vector<int> b;
-  cut(hi, &b);
-  return b;
-}
-
 // Makes the device table of balanced ranges of an axis match range length
 // `len` (as many ranges as uniform ranges of len would give); synchronous,
 // so never called while a graph is being captured.
@@ -278,17 +224,10 @@ shasta_status ensure_ranges(shasta_ctx* c, int axis, long long len, int variant)
   const long long n = axis == 0 ? c->g.nx : (axis == 1 ? c->g.ny : c->g.nz);
   const long long total = work_positions(c, axis);
   const long long R = (total + len - 1) / len;
-  // range r runs on warp r mod W of the launch (W = resident warps of one
-  // wave, blocks handed to the SMs in order), in the CTA of launch rank
-  // (r mod W) / wpb / SMs on its SM
   const int wpsm = c->occ[c->eos.kind][axis][variant];
   const long long K = wpsm > 0 ? wpsm / c->wpb : 1;  // CTAs per SM
-  const long long W = (long long)c->sm_count * K * c->wpb;
-  const double skew = K > 1 ? c->rank_skew[axis] : 0.0;
-  auto weight = [&](long long r) {
-    const long long rank = (r % W) / c->wpb / c->sm_count;
-    return 1.0 + skew * (1.0 - 2.0 * (double)rank / (double)(K - 1 > 0 ? K - 1 : 1));
-  };
+  const double skew = c->rank_skew[axis];
+  auto weight = [&](long long r) { return rank_weight(r, c->sm_count, K, c->wpb, skew); };
   const std::vector<int> b = balanced_bounds(total, n, R, axis == 0 ? 8 : 1, 13.0, c->edge_cost, weight);
   drop_graph(c);  // a captured graph holds the old table and its size
   c->ranges_len[axis] = 0;
