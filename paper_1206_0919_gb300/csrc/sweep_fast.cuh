@@ -405,18 +405,21 @@ __device__ __forceinline__ unsigned rec32(float E, float mx, float my, float mz,
   if constexpr (EOS == EOS_TABLE) {
     pp = table_p32(T, E, M2);
   } else if constexpr (EOS == EOS_BAG) {
-    // One root for both branches.  The ideal-gas root e lies above e_c
-    // exactly when (E - e_c)(E + e_c/3) > |M|^2, i.e. 3D > e_c (2E + e_c);
-    // then the bag root with p = (e - 4b)/3, else b = 0, which is the
-    // ideal-gas root itself (p = D / (E + sqrt(E^2 + 3D))):
-    //   e + ... : p = (D - 4bE/3) / (E - 2b + sqrt(3D + (E - 4b)^2 - 12b^2)) - 4b/3.
+    // One root for both branches.  With R0 = E^2 + 3D the ideal-gas root
+    // e = sqrt(R0) - E lies above e_c exactly when R0 > (E + e_c)^2; then
+    // the bag root with p = (e - 4b)/3, else b = 0, which is the ideal-gas
+    // root itself (p = D / (E + sqrt(R0))):
+    //   p = (D - 4bE/3) / (E - 2b + sqrt(r)) - 4b/3,  r = R0 - 4b (2E - b)
+    // (r = 3D + (E - 4b)^2 - 12b^2).
     D = fmaxf(D, 0.0f);
-    const bool bag = 3.0f * D > ec * fmaf(2.0f, E, ec);
+    const float R0 = fmaf(3.0f, D, E2);
+    const float te = E + ec;
+    const bool bag = R0 > te * te;
     const float b = bag ? B : 0.0f;
-    const float q = fmaf(-4.0f, b, E);
-    const float r = fmaf(3.0f, D, fmaf(q, q, -12.0f * (b * b)));
+    const float r = fmaf(-4.0f * b, fmaf(2.0f, E, -b), R0);
     const float s = sqrtf(fmaxf(r, 0.0f));
-    pp = fmaf(-(4.0f / 3.0f) * b, E, D) * __fdividef(1.0f, fmaf(-2.0f, b, E + s)) - (4.0f / 3.0f) * b;
+    const float b43 = (4.0f / 3.0f) * b;
+    pp = fmaf(fmaf(-b43, E, D), __fdividef(1.0f, fmaf(-2.0f, b, E + s)), -b43);
     // the bag root must exist and lie above e_c; else the mixed-phase point
     if (bag && !(E > ec && r >= 0.0f && fmaf(3.0f, pp, 4.0f * B) > ec))
       pp = __fdividef(M2, E - ec) - E;
