@@ -120,9 +120,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def committed_traffic(precision, grid):
-    """DRAM bytes per sweep launch from the committed ncu summary, if it was
-    taken on the current kernel sources; else None."""
+def committed_figure(name, precision, grid):
+    """A per-launch figure (`traffic_per_launch`: DRAM bytes; `inst_per_cell`:
+    warp-instructions per cell) from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
     path = os.path.join(ROOT, "profiles", "sweep_kernel_hot_spots.md")
     try:
         text = open(path).read()
@@ -131,8 +132,13 @@ def committed_traffic(precision, grid):
     src = re.search(r"kernel sources sha256\[:16\]:\s*([0-9a-f]{16})", text)
     if not src or src.group(1) != kernel_source_hash():
         return None
-    m = re.search(rf"traffic_per_launch\[{precision},{grid}\]:\s*([0-9.eE+]+)", text)
+    m = re.search(rf"{name}\[{precision},{grid}\]:\s*([0-9.eE+]+)", text)
     return float(m.group(1)) if m else None
+
+
+def committed_traffic(precision, grid):
+    """DRAM bytes per sweep launch from the committed ncu summary (or None)."""
+    return committed_figure("traffic_per_launch", precision, grid)
 
 
 class ClockSampler:
@@ -416,6 +422,21 @@ def run_ours(args):
                 "launch_us": launch_s * 1e6,
                 "timed": "CUDA events around the 200 split steps of every timed event"}
 
+    # the same launches against the instruction-issue roof (the bound of this
+    # kernel): warp-instructions per cell from the committed capture on the
+    # current sources, 4 schedulers per SM at the sampled SM clock
+    ipc = committed_figure("inst_per_cell", args.precision, N)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz")
+    issue_roof = None
+    if ipc and mhz:
+        issue_peak = sms * 4 * mhz * 1e6
+        issue_ach = ipc * ncell / launch_s
+        issue_roof = {"bound": "issue", "achieved": issue_ach, "peak": issue_peak,
+                      "unit": "warp-instructions/s", "frac": issue_ach / issue_peak,
+                      "inst_per_cell": ipc, "peak_from": f"{sms} SMs x 4 schedulers x {mhz:.0f} MHz",
+                      "inst_from": "smsp__inst_executed.sum of the committed capture, mean of the axes"}
+
     tuning = {"xyz"[a]: {"variant": v, "range_len": r} for a, (v, r) in enumerate(solver.tuning())}
 
     # per-axis sweep durations (after the timed region)
@@ -520,7 +541,7 @@ def run_ours(args):
             "dtype": {"fp32": "f32", "mixed": "f32+f64", "mixed_fp64": "f32+f64",
                       "fp64": "f64"}[args.precision],
             "data": "synthetic", "config": cfg,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "roofline_issue": issue_roof, "cpu_baseline": cpu, "e2e": e2e,
             # per event: 600 sweeps, the input check and five conversions
             "gpu_launches": (3 * EVENT_STEPS + 6) * args.steps, "clocks": clocks,
             "tuning": tuning,

@@ -65,3 +65,22 @@ def test_oracle_rate_sample_is_bounded(monkeypatch):
     calls.clear()
     rate, threads, steps, t = bench.oracle_rate(4, max_steps=5, target_s=1e9, threads=1)
     assert steps == 5 and calls == [0, 1, 2, 3, 4]
+
+
+def test_committed_figures_only_for_the_current_kernel_sources(tmp_path, monkeypatch):
+    """The roofline's traffic and instruction counts come from the committed
+    ncu summary only while its kernel-source hash is that of the sources."""
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "sweep_kernel_hot_spots.md").write_text(
+        "kernel sources sha256[:16]: 0123456789abcdef\n"
+        "traffic_per_launch[fp32,200]: 3.10e8\n"
+        "inst_per_cell[fp32,200]: 11.05\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0123456789abcdef")
+    assert bench.committed_traffic("fp32", 200) == 3.1e8
+    assert bench.committed_figure("inst_per_cell", "fp32", 200) == 11.05
+    assert bench.committed_figure("inst_per_cell", "fp32", 256) is None
+    assert bench.committed_figure("inst_per_cell", "mixed", 200) is None
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "fedcba9876543210")
+    assert bench.committed_traffic("fp32", 200) is None
+    assert bench.committed_figure("inst_per_cell", "fp32", 200) is None
