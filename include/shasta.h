@@ -194,9 +194,11 @@ shasta_status shasta_sweep(shasta_ctx* ctx, int axis);
  * sweep's positions, line groups of 32 lines x positions along the axis, are
  * cut into as many ranges as that length gives, handed to the resident warps;
  * the cuts balance each range's streaming cost, its cells plus a 13-position
- * halo per line it touches, unless the environment sets SHASTA_BALANCE=0).
- * FP64: the length of the line segments streamed one per thread.  No choice
- * changes results.
+ * halo per line it touches and about 11 per line end, unless the environment
+ * sets SHASTA_BALANCE=0), and the share of work of the CTAs resident on one
+ * SM by launch order (1 + s for the first, 1 - s for the last, s timed among
+ * 0, 0.04 and 0.08 unless SHASTA_RANK_SKEW sets it).  FP64: the length of the
+ * line segments streamed one per thread.  No choice changes results.
  * Runs sweeps from the current state into the spare buffer only, so the
  * state is unchanged; synchronous.  Errors: EINVAL (state not set), ECUDA. */
 shasta_status shasta_autotune(shasta_ctx* ctx);
