@@ -275,9 +275,10 @@ def test_clamp_counter():
 
 @pytest.mark.parametrize("precision", ["fp32", "mixed", "mixed_fp64", "fp64"])
 def test_graphs_and_launch_choices_bitwise(monkeypatch, precision):
-    """CUDA-graph replay, the autotuner, balanced and uniform work ranges and
-    every forced launch choice (work range length, register variant; FP64:
-    line segment length) give bitwise identical states."""
+    """CUDA-graph replay, the autotuner, balanced work ranges (any work shares
+    by CTA launch rank, any line-end cost) and uniform ones, and every forced
+    launch choice (work range length, register variant; FP64: line segment
+    length) give bitwise identical states."""
     shape = (72, 56, 48)
     pr = W.hot_spots(shape=shape, seed=21, n_spots=6, sigma=(2.0, 4.0), radial_flow=0.1)
     O = oracle()
@@ -296,6 +297,13 @@ def test_graphs_and_launch_choices_bitwise(monkeypatch, precision):
     outs.append(run(autotune=False, use_graphs=True))
     outs.append(run(autotune=True, use_graphs=False))
     monkeypatch.delenv("SHASTA_BALANCE")
+    # balanced ranges with other work shares by CTA launch rank and line-end costs
+    for skew, edge in (("0", "0"), ("0.2", "40"), ("0.45", "11")):
+        monkeypatch.setenv("SHASTA_RANK_SKEW", skew)
+        monkeypatch.setenv("SHASTA_EDGE_COST", edge)
+        outs.append(run(autotune=False, use_graphs=True))
+    monkeypatch.delenv("SHASTA_RANK_SKEW")
+    monkeypatch.delenv("SHASTA_EDGE_COST")
     # forced work ranges (FP64: segment lengths, whole lines for 100000)
     for rng, var in ((100000, 0), (37, 1), (24, 0), (5, 1)):
         monkeypatch.setenv("SHASTA_RANGE", str(rng))
