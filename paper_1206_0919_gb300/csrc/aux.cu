@@ -96,9 +96,12 @@ __global__ void k_recover(Rec6 r, size_t n, EosParams q) {
         eos_solve<double, EOS_BAG>(E, M, q.B, q.ec, e, pp);
       else
         eos_solve<double, EOS_IDEAL>(E, M, q.B, q.ec, e, pp);
-      double h = E + pp;
-      for (int a = 0; a < 3; ++a) v[a] = ((scale == 1.0) ? m[a] : m[a] * scale) / h;
-      nb = R * sqrt((e + pp) / h);
+      // v = M / (E + p) and n = R sqrt(1 - v^2) = R sqrt((e + p) / (E + p))
+      // with one reciprocal of E + p (the quotients within an ulp of the
+      // divisions; the state itself never depends on them)
+      const double ih = 1.0 / (E + pp);
+      for (int a = 0; a < 3; ++a) v[a] = ((scale == 1.0) ? m[a] : m[a] * scale) * ih;
+      nb = R * sqrt((e + pp) * ih);
     }
     if (r.out[0]) r.out[0][i] = e;
     if (r.out[1]) r.out[1][i] = v[0];
