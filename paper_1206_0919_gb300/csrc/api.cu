@@ -300,6 +300,7 @@ SweepParams sweep_params(shasta_ctx* c, int axis, int from, int variant, long lo
   P.bag_ec = c->eos.e_c;
   P.clamp_count = c->d_count;
   P.tab = c->tab;
+  set_float_scalars(P);
   P.range_len = range < 1 ? 1 : range;  // FP64: cells per line segment
   P.variant = variant;
   if (c->o.precision != SHASTA_FP64) {

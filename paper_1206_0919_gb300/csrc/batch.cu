@@ -368,6 +368,7 @@ SweepParams batch_params(const shasta_batch* b, const LaunchRec& L, int from, in
   P.rout = b->rf[from ^ 1];
   P.eta = b->o.eta;
   P.omd = 1.0 - b->o.delta;
+  set_float_scalars(P);
   P.variant = variant;
   P.range_len = range < 1 ? 0 : range;
   P.plane = 1;

@@ -82,7 +82,24 @@ struct SweepParams {
   float* qout;
   float* rout;
   EosTable tab;  // EOS_TABLE only
+  // fast kernels: the scalars above rounded to float (set_float_scalars), so
+  // that the kernels take them as constant-bank operands instead of holding
+  // converted copies in registers
+  float f_tau_h, f_tau_f, f_htau_h, f_htau_f, f_eta, f_omd, f_bag_B, f_bag_ec;
 };
+
+// Fills the float copies of the launch scalars (host side, after the
+// doubles are set).
+inline void set_float_scalars(SweepParams& P) {
+  P.f_tau_h = (float)P.tau_h;
+  P.f_tau_f = (float)P.tau_f;
+  P.f_htau_h = (float)P.htau_h;
+  P.f_htau_f = (float)P.htau_f;
+  P.f_eta = (float)P.eta;
+  P.f_omd = (float)P.omd;
+  P.f_bag_B = (float)P.bag_B;
+  P.f_bag_ec = (float)P.bag_ec;
+}
 
 // Batched sweeps: one event of a batch.  All events of a batch share the
 // batch's state arrays (qin/rin/qout/rout of SweepParams); the event's cells

@@ -184,12 +184,12 @@ struct GeoP {
   __device__ __forceinline__ int nb() const { return P.nb; }
   __device__ __forceinline__ int bc() const { return P.bc; }
   __device__ __forceinline__ const float* frozen() const { return static_cast<const float*>(P.frozen); }
-  __device__ __forceinline__ float tau_h() const { return float(P.tau_h); }
-  __device__ __forceinline__ float tau_f() const { return float(P.tau_f); }
-  __device__ __forceinline__ float htau_h() const { return float(P.htau_h); }
-  __device__ __forceinline__ float htau_f() const { return float(P.htau_f); }
-  __device__ __forceinline__ float B() const { return float(P.bag_B); }
-  __device__ __forceinline__ float ec() const { return float(P.bag_ec); }
+  __device__ __forceinline__ float tau_h() const { return P.f_tau_h; }
+  __device__ __forceinline__ float tau_f() const { return P.f_tau_f; }
+  __device__ __forceinline__ float htau_h() const { return P.f_htau_h; }
+  __device__ __forceinline__ float htau_f() const { return P.f_htau_f; }
+  __device__ __forceinline__ float B() const { return P.f_bag_B; }
+  __device__ __forceinline__ float ec() const { return P.f_bag_ec; }
 };
 struct GeoR {
   ItemGeo g;
@@ -647,8 +647,8 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, i
   if (i2 < i1) i2 = i1;
 
   const float tau_h = G.tau_h(), tau_f = G.tau_f();
-  const float eta = float(P.eta);
-  const float omd = float(P.omd), B = G.B(), ec = G.ec();
+  const float eta = P.f_eta;
+  const float omd = P.f_omd, B = G.B(), ec = G.ec();
   const float htau_h = G.htau_h(), htau_f = G.htau_f();
   const f2 eta2 = pk(eta, eta), m8c = pk(-0.125f, -0.125f);
   const f2 ht_h2 = pk(htau_h, htau_h), ht_f2 = pk(htau_f, htau_f);
