@@ -355,7 +355,10 @@ def run_ours(args):
     N = args.grid
     ncell = N ** 3
     prims = workload_prims(N, seed=workload_seed(rank))
-    stream = torch.cuda.Stream()
+    # the steps run on streams of raised priority; the library's set / get
+    # copies and conversions run on its own stream of the lowest priority,
+    # so that on the end-to-end leg they yield the SMs to the other event's steps
+    stream = torch.cuda.Stream(priority=-1)
     solver = S.Solver((N, N, N), precision=args.precision, stream=stream.cuda_stream,
                       device=local)
     # the event's initial conserved state, resident on the device in FP64
@@ -459,7 +462,7 @@ def run_ours(args):
     # the newer one runs.
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
     host_in = [pin(a) for a in prims.as_list()]
-    stream2 = torch.cuda.Stream()
+    stream2 = torch.cuda.Stream(priority=-1)
     solver2 = S.Solver((N, N, N), precision=args.precision, stream=stream2.cuda_stream,
                        device=local)
     ctxs = (solver, solver2)

@@ -161,8 +161,13 @@ shasta_status shasta_destroy(shasta_ctx* ctx);
 
 /* Sets the conserved state (Sec. 2, Eqs. cf-density, cf-momentum,
  * cf-energy).  Five arrays of nx*ny*nz doubles in memory space mem.  Resets
- * the step counter to 0.  Errors: EINVAL (NULL pointer or bad mem),
- * EUNPHYSICAL (check_input set and the state is not physical), ECUDA. */
+ * the step counter to 0.  The copy, input check and conversion run on the
+ * context's own transfer stream, created at the lowest stream priority: they
+ * start after the work already enqueued on the context's stream, and work
+ * enqueued there afterwards waits for them (a caller whose compute streams
+ * have a higher priority keeps the SMs for them while transfers overlap).
+ * Errors: EINVAL (NULL pointer or bad mem), EUNPHYSICAL (check_input set and
+ * the state is not physical; the state is left as it was), ECUDA. */
 shasta_status shasta_set_conserved(shasta_ctx* ctx, const double* E, const double* Mx,
                                    const double* My, const double* Mz, const double* R,
                                    int mem);
@@ -211,12 +216,15 @@ shasta_status shasta_get_tuning(const shasta_ctx* ctx, int out[6]);
 shasta_status shasta_sync(shasta_ctx* ctx);
 
 /* Copies the conserved state out (five arrays, any may be NULL to skip).
- * Synchronous with respect to the context's stream. */
+ * Synchronous with respect to the context's stream: it waits for the work
+ * enqueued there, then converts and copies on the transfer stream (see
+ * shasta_set_conserved) and returns when the arrays are filled. */
 shasta_status shasta_get_conserved(shasta_ctx* ctx, double* E, double* Mx, double* My,
                                    double* Mz, double* R, int mem);
 
 /* Recovers and copies out the primitives e, vx, vy, vz, n, p of the current
- * state (Sec. 3 phases 3-4; any pointer may be NULL to skip).  Synchronous. */
+ * state (Sec. 3 phases 3-4; any pointer may be NULL to skip).  Synchronous,
+ * on the transfer stream as shasta_get_conserved. */
 shasta_status shasta_get_primitives(shasta_ctx* ctx, double* e, double* vx, double* vy,
                                     double* vz, double* n, double* p, int mem);
 

@@ -68,6 +68,12 @@ struct shasta_ctx {
   double* h_small = nullptr;              // pinned: 5 totals + counters
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // set / get: copies and format conversions run on a stream of the lowest
+  // priority, ordered after the context stream's earlier work and before its
+  // later work by two events, so that a caller's higher-priority compute
+  // streams keep the SMs while they overlap
+  cudaStream_t xfer = nullptr;
+  cudaEvent_t ev_main = nullptr, ev_xfer = nullptr;
   int64_t steps = 0;
   int sm_count = 152;
   int occ[3][3][2] = {};  // FP32 / MIXED: resident warps per SM [eos][axis][variant]
@@ -147,7 +153,8 @@ shasta_status ensure_staging(shasta_ctx* c) {
 
 // Copies five caller arrays into device doubles: returns device pointers
 // (the caller's own for DEVICE memory, the staging area for HOST memory).
-shasta_status stage_in(shasta_ctx* c, const double* const src[5], int mem, const double* out[5]) {
+shasta_status stage_in(shasta_ctx* c, const double* const src[5], int mem, const double* out[5],
+                       cudaStream_t st) {
   if (mem == SHASTA_MEM_DEVICE) {
     for (int k = 0; k < 5; ++k) out[k] = src[k];
     return SHASTA_OK;
@@ -156,30 +163,45 @@ shasta_status stage_in(shasta_ctx* c, const double* const src[5], int mem, const
   if (s != SHASTA_OK) return s;
   for (int k = 0; k < 5; ++k) {
     double* d = c->staging + (size_t)k * c->ncell;
-    CK(cudaMemcpyAsync(d, src[k], c->ncell * sizeof(double), cudaMemcpyHostToDevice, c->stream),
+    CK(cudaMemcpyAsync(d, src[k], c->ncell * sizeof(double), cudaMemcpyHostToDevice, st),
        "cudaMemcpyAsync H2D");
     out[k] = d;
   }
   return SHASTA_OK;
 }
 
-shasta_status check_count(shasta_ctx* c, bool prims, const double* const f[5]) {
-  CK(cudaMemsetAsync(c->d_count + 1, 0, sizeof(unsigned long long), c->stream), "memset");
+shasta_status check_count(shasta_ctx* c, bool prims, const double* const f[5], cudaStream_t st) {
+  CK(cudaMemsetAsync(c->d_count + 1, 0, sizeof(unsigned long long), st), "memset");
   if (prims)
-    CK(launch_check_prims(f, c->ncell, c->d_count + 1, c->stream), "check_prims");
+    CK(launch_check_prims(f, c->ncell, c->d_count + 1, st), "check_prims");
   else
-    CK(launch_check_cons(f, c->ncell, c->d_count + 1, c->stream), "check_cons");
+    CK(launch_check_cons(f, c->ncell, c->d_count + 1, st), "check_cons");
   unsigned long long* h = reinterpret_cast<unsigned long long*>(c->h_small + 8);
-  CK(cudaMemcpyAsync(h, c->d_count + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                     c->stream),
+  CK(cudaMemcpyAsync(h, c->d_count + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st),
      "memcpy count");
-  CK(cudaStreamSynchronize(c->stream), "sync");
+  CK(cudaStreamSynchronize(st), "sync");
   if (*h) {
     char m[160];
     snprintf(m, sizeof m, "%llu cells are not physical (non-finite, %s)", *h,
              prims ? "e < 0, n < 0 or |v| >= 1" : "E < 0 or |M| >= E");
     return fail(c, SHASTA_EUNPHYSICAL, m);
   }
+  return SHASTA_OK;
+}
+
+// The transfer stream starts after the work enqueued so far on the context
+// stream (a set must not overwrite a state still being swept; a get reads the
+// state the steps leave) ...
+shasta_status xfer_begin(shasta_ctx* c) {
+  CK(cudaEventRecord(c->ev_main, c->stream), "event record");
+  CK(cudaStreamWaitEvent(c->xfer, c->ev_main, 0), "stream wait");
+  return SHASTA_OK;
+}
+
+// ... and the context stream's later work waits for what it enqueued.
+shasta_status xfer_end(shasta_ctx* c) {
+  CK(cudaEventRecord(c->ev_xfer, c->xfer), "event record");
+  CK(cudaStreamWaitEvent(c->stream, c->ev_xfer, 0), "stream wait");
   return SHASTA_OK;
 }
 
@@ -524,6 +546,7 @@ shasta_status autotune(shasta_ctx* c) {
 void release(shasta_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->xfer) cudaStreamSynchronize(c->xfer);
   cudaFree(c->state_mem);
   cudaFree(c->split_mem);
   cudaFree(c->tab_mem);
@@ -535,6 +558,9 @@ void release(shasta_ctx* c) {
   for (int a = 0; a < 3; ++a) cudaFree(c->d_ranges[a]);
   cudaFreeHost(c->h_small);
   drop_graph(c);
+  if (c->xfer) cudaStreamDestroy(c->xfer);
+  if (c->ev_main) cudaEventDestroy(c->ev_main);
+  if (c->ev_xfer) cudaEventDestroy(c->ev_xfer);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -757,6 +783,14 @@ shasta_status shasta_create(const shasta_grid* g, double dx, double lambda, cons
     if (err != cudaSuccess) return bail(err, "cudaStreamCreate");
     c->own_stream = true;
   }
+  {
+    int least = 0, greatest = 0;
+    err = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (err == cudaSuccess) err = cudaStreamCreateWithPriority(&c->xfer, cudaStreamNonBlocking, least);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&c->ev_main, cudaEventDisableTiming);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&c->ev_xfer, cudaEventDisableTiming);
+    if (err != cudaSuccess) return bail(err, "transfer stream");
+  }
   *out = c;
   return SHASTA_OK;
 }
@@ -776,17 +810,19 @@ shasta_status shasta_set_conserved(shasta_ctx* c, const double* E, const double*
   DeviceGuard dg(c->device);
   const double* src[5] = {E, Mx, My, Mz, R};
   const double* d[5];
-  shasta_status s = stage_in(c, src, mem, d);
+  shasta_status s = xfer_begin(c);
+  if (s == SHASTA_OK) s = stage_in(c, src, mem, d, c->xfer);
   if (s != SHASTA_OK) return s;
   if (c->o.check_input) {
-    s = check_count(c, false, d);
+    s = check_count(c, false, d, c->xfer);
     if (s != SHASTA_OK) return s;
   }
   c->cur = 0;
   for (int k = 0; k < 5; ++k)
-    CK(launch_from_f64(d[k], c->view[0].p[k], c->view[0].s[k], c->ncell, c->is32, c->stream),
+    CK(launch_from_f64(d[k], c->view[0].p[k], c->view[0].s[k], c->ncell, c->is32, c->xfer),
        "convert in");
-  return after_set(c);
+  s = xfer_end(c);
+  return s == SHASTA_OK ? after_set(c) : s;
 }
 
 shasta_status shasta_set_primitives(shasta_ctx* c, const double* e, const double* vx,
@@ -797,15 +833,17 @@ shasta_status shasta_set_primitives(shasta_ctx* c, const double* e, const double
   DeviceGuard dg(c->device);
   const double* src[5] = {e, vx, vy, vz, n};
   const double* d[5];
-  shasta_status s = stage_in(c, src, mem, d);
+  shasta_status s = xfer_begin(c);
+  if (s == SHASTA_OK) s = stage_in(c, src, mem, d, c->xfer);
   if (s != SHASTA_OK) return s;
   if (c->o.check_input) {
-    s = check_count(c, true, d);
+    s = check_count(c, true, d, c->xfer);
     if (s != SHASTA_OK) return s;
   }
   c->cur = 0;
-  CK(launch_prim2cons(d, c->view[0], c->ncell, c->is32, eos_params(c), c->stream), "prim2cons");
-  return after_set(c);
+  CK(launch_prim2cons(d, c->view[0], c->ncell, c->is32, eos_params(c), c->xfer), "prim2cons");
+  s = xfer_end(c);
+  return s == SHASTA_OK ? after_set(c) : s;
 }
 
 shasta_status shasta_step(shasta_ctx* c, int nsteps) {
@@ -902,17 +940,19 @@ shasta_status shasta_get_conserved(shasta_ctx* c, double* E, double* Mx, double*
     shasta_status s = ensure_staging(c);
     if (s != SHASTA_OK) return s;
   }
+  shasta_status s = xfer_begin(c);
+  if (s != SHASTA_OK) return s;
   for (int k = 0; k < 5; ++k) {
     if (!dst[k]) continue;
     double* d = mem == SHASTA_MEM_DEVICE ? dst[k] : c->staging + (size_t)k * c->ncell;
     CK(launch_to_f64(c->view[c->cur].p[k], c->view[c->cur].s[k], d, c->ncell, c->is32,
-                     c->stream),
+                     c->xfer),
        "convert out");
     if (mem == SHASTA_MEM_HOST)
-      CK(cudaMemcpyAsync(dst[k], d, c->ncell * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+      CK(cudaMemcpyAsync(dst[k], d, c->ncell * sizeof(double), cudaMemcpyDeviceToHost, c->xfer),
          "cudaMemcpyAsync D2H");
   }
-  CK(cudaStreamSynchronize(c->stream), "sync");
+  CK(cudaStreamSynchronize(c->xfer), "sync");
   return SHASTA_OK;
 }
 
@@ -930,14 +970,16 @@ shasta_status shasta_get_primitives(shasta_ctx* c, double* e, double* vx, double
   }
   for (int k = 0; k < 6; ++k)
     d[k] = !dst[k] ? nullptr : (mem == SHASTA_MEM_DEVICE ? dst[k] : c->staging + (size_t)k * c->ncell);
-  CK(launch_recover(c->view[c->cur], d, c->ncell, c->is32, eos_params(c), c->stream), "recover");
+  shasta_status s = xfer_begin(c);
+  if (s != SHASTA_OK) return s;
+  CK(launch_recover(c->view[c->cur], d, c->ncell, c->is32, eos_params(c), c->xfer), "recover");
   if (mem == SHASTA_MEM_HOST)
     for (int k = 0; k < 6; ++k)
       if (dst[k])
         CK(cudaMemcpyAsync(dst[k], d[k], c->ncell * sizeof(double), cudaMemcpyDeviceToHost,
-                           c->stream),
+                           c->xfer),
            "cudaMemcpyAsync D2H");
-  CK(cudaStreamSynchronize(c->stream), "sync");
+  CK(cudaStreamSynchronize(c->xfer), "sync");
   return SHASTA_OK;
 }
 
