@@ -388,3 +388,39 @@ def test_mixed_recovery_at_high_gamma(gamma):
     assert max(err.values()) <= 2 * yard, info
     if gamma <= 10.0:
         assert max(err.values()) <= 1e-4, info
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_rejected_set_keeps_the_state(precision):
+    """A set refused for unphysical input (checked before any conversion, on
+    the transfer stream) leaves the previous state and the step counter's
+    work intact: stepping on afterwards gives the same state as without the
+    refused call; and steps enqueued right after a set run on the new state."""
+    shape = (24, 20, 16)
+    pr = W.hot_spots(shape=shape, seed=31, n_spots=4, sigma=(2.0, 3.0))
+    O = oracle()
+    U0 = O.prim2cons(OR.params(shape), *pr.as_list())
+    bad = [u.copy() for u in U0]
+    bad[1][3, 2, 1] = 2.0 * bad[0][3, 2, 1]  # |M| > E
+    outs = []
+    for refuse in (False, True):
+        with S.Solver(shape, precision=precision) as s:
+            s.set_conserved(U0)
+            s.step(3)  # enqueued, not waited for
+            if refuse:
+                with pytest.raises(S.ShastaError) as ei:
+                    s.set_conserved(bad)
+                assert ei.value.status == S.EUNPHYSICAL
+            s.step(4)
+            outs.append(s.get_conserved())
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+    # a set right behind pending steps replaces the state they leave
+    with S.Solver(shape, precision=precision) as s:
+        s.set_conserved(U0)
+        s.step(5)
+        s.set_conserved(U0)
+        s.step(7)
+        got = s.get_conserved()
+    for a, b in zip(got, outs[0]):
+        assert np.array_equal(a, b)
