@@ -523,7 +523,7 @@ def run_ours(args):
         extra["alu_peaks"] = alu_peaks(local, stream)
         extra["batch64"] = batch_leg(ranks, stream, local, n_events=64, precision="mixed",
                                      steps=100, warmup=12)
-        extra["serve"] = serve_legs(args, ranks, local, rates=(60.0, 200.0), n_events=150)
+        extra["serve"] = serve_legs(args, ranks, local, rates=(60.0, 200.0), n_events=300)
 
     del U0
     cpu = None
@@ -982,8 +982,10 @@ def serve_stream_leg(ranks, local, inputs, rate, n_events, precision, budget_gb=
     }
 
 
-def serve_legs(args, ranks, local, rates=(60.0, 200.0), n_events=150):
-    """Config 4 on the headline line: short Poisson streams at each rate."""
+def serve_legs(args, ranks, local, rates=(60.0, 200.0), n_events=300):
+    """Config 4 on the headline line: Poisson streams of 300 events at each
+    rate (long enough for the served rate to settle past the stream's ramp-up
+    and tail)."""
     inputs = serve_inputs()
     precision = "mixed" if args.precision == "mixed" else "fp32"  # servers run FP32 or MIXED
     out = {"workload": "serve_poisson",

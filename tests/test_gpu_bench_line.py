@@ -35,6 +35,11 @@ def test_headline_line_keys_and_legs():
     rf = d["roofline"]
     assert rf["bound"] == "hbm" and rf["unit"] == "GB/s" and 0.05 < rf["frac"] < 1.2
     assert rf["frac"] == pytest.approx(rf["achieved"] / rf["peak"])
+    # the instruction-issue roof, when the committed capture matches the sources
+    ri = d["roofline_issue"]
+    if ri is not None:
+        assert ri["bound"] == "issue" and 0.05 < ri["frac"] < 1.05
+        assert ri["frac"] == pytest.approx(ri["achieved"] / ri["peak"])
     e2e = d["e2e"]
     assert e2e["h2d_bytes_per_step"] == 40 * 200 ** 3 and e2e["d2h_bytes_per_step"] == 48 * 200 ** 3
     assert 0.2 * d["value"] < e2e["value"] < 1.2 * d["value"]
@@ -51,7 +56,7 @@ def test_headline_line_keys_and_legs():
         assert 0 < acc["max_ratio_to_spread"] < 100 and acc["max_rel_l1_e"] < 0.05
     for rate in ("60_per_s", "200_per_s"):
         s = d["serve"][rate]
-        assert s["events"] == 150 and s["value"] > 1.0
+        assert s["events"] == 300 and s["value"] > 1.0
         assert 0 < s["latency_s"]["p50"] <= s["latency_s"]["p99"]
     p = d["precisions"]
     assert p["mixed"]["value"] > 1e9 and p["mixed_fp64"]["value"] > 1e8
