@@ -110,6 +110,11 @@ shasta_status shasta_batch_set_step_counter(shasta_batch* b, int id, int64_t ste
  * shasta_counters).  Synchronous. */
 shasta_status shasta_batch_counters(shasta_batch* b, int id, int64_t out[1]);
 
+/* Checked builds only: as shasta_checked_report, for the batched sweeps of
+ * all events (waits for the whole device).  Errors: EINVAL (NULL arguments,
+ * or a library built without the checks), ECUDA. */
+shasta_status shasta_batch_checked_report(shasta_batch* b, unsigned long long out[3]);
+
 /* out[0] resident events, out[1] cells in use, out[2] capacity in cells,
  * out[3] largest free run of cells, out[4] kernel launches per step of the
  * current work lists, out[5] work items per step, out[6] sweep kernel

@@ -21,6 +21,11 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libshasta.so")
+# checked build: the same library with every global and shared-memory access
+# of the FP32 / MIXED sweeps bounds-tested (refused accesses are counted and
+# skipped; shasta_checked_report reads the record); for tests, not for speed
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "libshasta_checked.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -62,10 +67,10 @@ def _deps_mtime() -> float:
     return max(m, os.path.getmtime(__file__))
 
 
-def _compile(unit, flags, verbose):
+def _compile(unit, flags, verbose, build_dir=BUILD, extra=()):
     src = os.path.join(CSRC, unit)
-    obj = os.path.join(BUILD, unit.replace(".cu", ".o"))
-    cmd = [nvcc()] + ARCH + COMMON + flags + ["-c", src, "-o", obj]
+    obj = os.path.join(build_dir, unit.replace(".cu", ".o"))
+    cmd = [nvcc()] + ARCH + COMMON + flags + list(extra) + ["-c", src, "-o", obj]
     if verbose:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -74,26 +79,30 @@ def _compile(unit, flags, verbose):
     return obj, r.stderr
 
 
-def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
-    """Compile every unit and link libshasta.so; returns its path."""
-    if not force and not verbose and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, jobs: int | None = None,
+          checked: bool = False) -> str:
+    """Compile every unit and link libshasta.so (checked: libshasta_checked.so,
+    built with -DSHASTA_CHECKED); returns its path."""
+    lib, build_dir = (LIB_CHECKED, BUILD_CHECKED) if checked else (LIB, BUILD)
+    extra = ("-DSHASTA_CHECKED",) if checked else ()
+    if not force and not verbose and os.path.exists(lib) and os.path.getmtime(lib) >= _deps_mtime():
+        return lib
+    os.makedirs(build_dir, exist_ok=True)
     jobs = jobs or min(len(UNITS), os.cpu_count() or 1)
     objs, logs = [], []
     with cf.ThreadPoolExecutor(jobs) as ex:
-        for obj, log in ex.map(lambda u: _compile(u[0], u[1], verbose), UNITS):
+        for obj, log in ex.map(lambda u: _compile(u[0], u[1], verbose, build_dir, extra), UNITS):
             objs.append(obj)
             logs.append(log)
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static", "-lrt", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     if verbose:
         sys.stderr.write("".join(logs))
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

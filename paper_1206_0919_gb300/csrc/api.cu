@@ -65,6 +65,7 @@ struct shasta_ctx {
   double* partials = nullptr;
   double* d_tot = nullptr;
   unsigned long long* d_count = nullptr;  // [0] clamp count, [1] check scratch
+  unsigned long long* d_chk = nullptr;    // checked builds: refused accesses [count, code, index]
   double* h_small = nullptr;              // pinned: 5 totals + counters
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -323,6 +324,14 @@ SweepParams sweep_params(shasta_ctx* c, int axis, int from, int variant, long lo
   P.clamp_count = c->d_count;
   P.tab = c->tab;
   set_float_scalars(P);
+  P.ncap = (long long)c->ncell;
+  P.chk = c->d_chk;  // null unless this is a checked build
+#ifdef SHASTA_CHECKED
+  // test aid of checked builds: a smaller bound on the state arrays (the
+  // accesses above it are then refused, which shows that the checks work)
+  if (const char* v = getenv("SHASTA_CHECKED_NCAP"))
+    if (atoll(v) > 0 && atoll(v) < P.ncap) P.ncap = atoll(v);
+#endif
   P.range_len = range < 1 ? 1 : range;  // FP64: cells per line segment
   P.variant = variant;
   if (c->o.precision != SHASTA_FP64) {
@@ -555,6 +564,7 @@ void release(shasta_ctx* c) {
   cudaFree(c->partials);
   cudaFree(c->d_tot);
   cudaFree(c->d_count);
+  cudaFree(c->d_chk);
   for (int a = 0; a < 3; ++a) cudaFree(c->d_ranges[a]);
   cudaFreeHost(c->h_small);
   drop_graph(c);
@@ -760,6 +770,11 @@ shasta_status shasta_create(const shasta_grid* g, double dx, double lambda, cons
   if (err != cudaSuccess) return bail(err, "cudaMalloc counters");
   err = cudaMemset(c->d_count, 0, 4 * sizeof(unsigned long long));
   if (err != cudaSuccess) return bail(err, "cudaMemset counters");
+#ifdef SHASTA_CHECKED
+  err = cudaMalloc((void**)&c->d_chk, 4 * sizeof(unsigned long long));
+  if (err == cudaSuccess) err = cudaMemset(c->d_chk, 0, 4 * sizeof(unsigned long long));
+  if (err != cudaSuccess) return bail(err, "check record");
+#endif
   err = cudaMallocHost((void**)&c->h_small, 16 * sizeof(double));
   if (err != cudaSuccess) return bail(err, "cudaMallocHost");
   if (opts.precision != SHASTA_FP64) {
@@ -1003,6 +1018,21 @@ shasta_status shasta_set_step_counter(shasta_ctx* c, int64_t steps) {
   if (steps < 0) return fail(c, SHASTA_EINVAL, "negative step counter");
   c->steps = steps;
   return SHASTA_OK;
+}
+
+shasta_status shasta_checked_report(shasta_ctx* c, unsigned long long out[3]) {
+  if (!c || !out) return SHASTA_EINVAL;
+#ifdef SHASTA_CHECKED
+  DeviceGuard dg(c->device);
+  unsigned long long h[4] = {};
+  CK(cudaStreamSynchronize(c->stream), "sync");
+  CK(cudaMemcpy(h, c->d_chk, sizeof h, cudaMemcpyDeviceToHost), "read the record");
+  CK(cudaMemset(c->d_chk, 0, sizeof h), "clear the record");
+  for (int k = 0; k < 3; ++k) out[k] = h[k];
+  return SHASTA_OK;
+#else
+  return fail(c, SHASTA_EINVAL, "not a checked build (built without SHASTA_CHECKED)");
+#endif
 }
 
 shasta_status shasta_counters(shasta_ctx* c, int64_t out[1]) {

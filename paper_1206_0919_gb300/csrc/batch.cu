@@ -59,6 +59,7 @@ struct shasta_batch {
   bool own_stream = false;
   long long cap = 0;
   void* pool = nullptr;
+  unsigned long long* d_chk = nullptr;  // checked builds: refused accesses [count, code, index]
   float* quad[2] = {};
   float* rf[2] = {};
   int cur = 0;
@@ -369,6 +370,8 @@ SweepParams batch_params(const shasta_batch* b, const LaunchRec& L, int from, in
   P.eta = b->o.eta;
   P.omd = 1.0 - b->o.delta;
   set_float_scalars(P);
+  P.ncap = b->cap;
+  P.chk = b->d_chk;  // null unless this is a checked build
   P.variant = variant;
   P.range_len = range < 1 ? 0 : range;
   P.plane = 1;
@@ -516,6 +519,7 @@ void release(shasta_batch* b) {
   cudaFree(b->staging);
   cudaFree(b->partials);
   cudaFree(b->d_tot);
+  cudaFree(b->d_chk);
   cudaFreeHost(b->h_small);
   for (int i = 0; i < shasta_batch::kSide; ++i) {
     if (b->side[i]) cudaStreamDestroy(b->side[i]);
@@ -609,6 +613,11 @@ shasta_status shasta_batch_create(const shasta_batch_opts* o, shasta_batch** out
   if (err != cudaSuccess) return bail(err, "cudaMalloc partials");
   err = cudaMalloc((void**)&b->d_tot, 8 * sizeof(double));
   if (err != cudaSuccess) return bail(err, "cudaMalloc totals");
+#ifdef SHASTA_CHECKED
+  err = cudaMalloc((void**)&b->d_chk, 4 * sizeof(unsigned long long));
+  if (err == cudaSuccess) err = cudaMemset(b->d_chk, 0, 4 * sizeof(unsigned long long));
+  if (err != cudaSuccess) return bail(err, "check record");
+#endif
   err = cudaMallocHost((void**)&b->h_small, 16 * sizeof(double));
   if (err != cudaSuccess) return bail(err, "cudaMallocHost");
   err = b->mixed ? prepare_batch_mixed(b->occ) : prepare_batch_f32(b->occ);
@@ -973,6 +982,21 @@ shasta_status shasta_batch_set_step_counter(shasta_batch* b, int id, int64_t ste
     b->plan_valid = false;
   }
   return SHASTA_OK;
+}
+
+shasta_status shasta_batch_checked_report(shasta_batch* b, unsigned long long out[3]) {
+  if (!b || !out) return SHASTA_EINVAL;
+#ifdef SHASTA_CHECKED
+  DeviceGuard dg(b->device);
+  unsigned long long h[4] = {};
+  CK(cudaDeviceSynchronize(), "sync");  // every side stream of the batch
+  CK(cudaMemcpy(h, b->d_chk, sizeof h, cudaMemcpyDeviceToHost), "read the record");
+  CK(cudaMemset(b->d_chk, 0, sizeof h), "clear the record");
+  for (int k = 0; k < 3; ++k) out[k] = h[k];
+  return SHASTA_OK;
+#else
+  return fail(b, SHASTA_EINVAL, "not a checked build (built without SHASTA_CHECKED)");
+#endif
 }
 
 shasta_status shasta_batch_counters(shasta_batch* b, int id, int64_t out[1]) {

@@ -86,6 +86,10 @@ struct SweepParams {
   // that the kernels take them as constant-bank operands instead of holding
   // converted copies in registers
   float f_tau_h, f_tau_f, f_htau_h, f_htau_f, f_eta, f_omd, f_bag_B, f_bag_ec;
+  // checked builds (SHASTA_CHECKED): cells in each of qin / rin / qout / rout,
+  // and the record [count, first code, first index] of refused accesses
+  long long ncap;
+  unsigned long long* chk;
 };
 
 // Fills the float copies of the launch scalars (host side, after the

@@ -56,6 +56,26 @@
 namespace shasta {
 namespace fast {
 
+// Checked builds (-DSHASTA_CHECKED): each global access of the streaming
+// sweeps, and each shared-memory access at a computed offset, is first
+// tested against the bounds of its buffer; a miss is counted in P.chk (count,
+// first code, first index) and the access is skipped.  The tests run them to
+// show that the index arithmetic stays in bounds; other builds compile the
+// tests away.  Codes: 1 state load, 2 frozen-ghost load, 3 state store,
+// 4 shared-memory ring, 5 range table.
+#ifdef SHASTA_CHECKED
+__device__ __forceinline__ bool chk_ok(unsigned long long* rec, bool ok, int code, long long idx) {
+  if (!ok && rec && atomicAdd(rec, 1ull) == 0ull) {
+    rec[1] = (unsigned long long)code;
+    rec[2] = (unsigned long long)idx;
+  }
+  return ok;
+}
+#define SH_OK(P, cond, code, idx) ::shasta::fast::chk_ok((P).chk, (cond), (code), (long long)(idx))
+#else
+#define SH_OK(P, cond, code, idx) true
+#endif
+
 constexpr int LANES = 32;
 constexpr int CH = 8;      // x sweep: positions per cooperative chunk
 constexpr int XSLOTS = 3;  // x sweep: chunk slots (previous, current, next)
@@ -260,6 +280,11 @@ __device__ __forceinline__ void copy_cell(const SweepParams& P, const Geo& G, fl
     const int side = q < 0 ? 0 : 1;
     int layer = q < 0 ? -1 - q : q - n;
     layer = layer > NG - 1 ? NG - 1 : layer;
+#ifdef SHASTA_CHECKED
+    const long long fi = (long long)(side * NG + layer) * NF * G.plane() + t;
+    if (!SH_OK(P, fi >= 0 && t < G.plane() && fi + 4 * G.plane() < 2LL * NG * NF * G.plane(), 2, fi))
+      return;
+#endif
     const float* fz = G.frozen() + (long long)(side * NG + layer) * NF * G.plane() + t;
 #pragma unroll
     for (int f = 0; f < 4; ++f) cp_async4(dq + f, fz + f * G.plane());
@@ -267,6 +292,7 @@ __device__ __forceinline__ void copy_cell(const SweepParams& P, const Geo& G, fl
     return;
   }
   const long long c = cell0 + (long long)map_pos(q, n, G.bc()) * stride;
+  if (!SH_OK(P, c >= 0 && c < P.ncap, 1, c)) return;
   cp_async16(dq, P.qin + 4 * c);
   cp_async4(dr, P.rin + c);
 }
@@ -654,6 +680,15 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, i
   const f2 ht_h2 = pk(htau_h, htau_h), ht_f2 = pk(htau_f, htau_f);
   const bool frozen = G.bc() == BC_FROZEN;
 
+#ifdef SHASTA_CHECKED
+  // whether nf floats at p lie in this warp's ring
+  auto sm_in = [&](const float* p, int nf) {
+    const long long o = p - wsm;
+    constexpr long long kRing = Smem<AXIS, RING>::per_warp;
+    return SH_OK(P, o >= 0 && o + nf <= kRing, 4, o);
+  };
+#endif
+
   auto x_slot = [&](int C) -> float* { return wsm + ((C + 3 * 4) % XSLOTS) * XSLOT; };
   // x path: cooperative copy of chunk C = positions [8C, 8C+8) of 32 rows
   // (the ghost variant, rare, stays a rolled loop: the x kernel is
@@ -678,6 +713,7 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, i
         long long tr = g * LANES + row;
         tr = tr < G.plane() ? tr : G.plane() - 1;
         const unsigned c = (unsigned)G.off() + (unsigned)tr * (unsigned)G.sb() + (unsigned)pos;
+        if (!SH_OK(P, (long long)c < P.ncap, 1, c)) continue;
         cp_async16(ring + row * XQSTR + pc * 4, P.qin + 4 * (size_t)c);
         cp_async4(ring + XQ + row * XRSTR + pc, P.rin + c);
       }
@@ -688,21 +724,34 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, i
   auto yz_issue = [&](float* slot, int q, bool ghost) {
     float* dq = slot + lane * 4;
     float* dr = slot + YQ + lane;
+#ifdef SHASTA_CHECKED
+    if (!sm_in(dq, 4) || !sm_in(dr, 1)) return;
+#endif
     if (ghost) {
       copy_cell(P, G, dq, dr, base, G.stride(), tl, q, n);
     } else {
       const unsigned c = base32 + (unsigned)q * stride32;
+      if (!SH_OK(P, (long long)c < P.ncap, 1, c)) return;
       cp_async16(dq, P.qin + 4 * (size_t)c);
       cp_async4(dr, P.rin + c);
     }
   };
   // quad (as the pairs (E, Mx), (My, Mz)) and R of a ring entry
   auto rdq = [&](const float* slot, int pos, f2& A, f2& Bp) {
+#ifdef SHASTA_CHECKED
+    if (!sm_in(XP ? slot + lane * XQSTR + pos * 4 : slot + lane * 4, 4)) {
+      A = Bp = pk(0.0f, 0.0f);
+      return;
+    }
+#endif
     const float4 v = *reinterpret_cast<const float4*>(XP ? slot + lane * XQSTR + pos * 4 : slot + lane * 4);
     A = pk(v.x, v.y);
     Bp = pk(v.z, v.w);
   };
   auto rdr = [&](const float* slot, int pos) -> float {
+#ifdef SHASTA_CHECKED
+    if (!sm_in(XP ? slot + XQ + lane * XRSTR + pos : slot + YQ + lane, 1)) return 0.0f;
+#endif
     return XP ? slot[XQ + lane * XRSTR + pos] : slot[YQ + lane];
   };
 
@@ -821,11 +870,15 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, i
         float o0, o1, o2, o3;
         up(oA, o0, o1);
         up(oB, o2, o3);
+#ifdef SHASTA_CHECKED
+        if (!sm_in(sjo + lane * XQSTR + pj * 4, 4) || !sm_in(sjo + XQ + lane * XRSTR + pj, 1)) return;
+#endif
         *reinterpret_cast<float4*>(sjo + lane * XQSTR + pj * 4) = make_float4(o0, o1, o2, o3);
         sjo[XQ + lane * XRSTR + pj] = oR;
       }
     } else if ((unsigned)(jo - s0) < span) {
       const unsigned c = base32 + (unsigned)jo * stride32;
+      if (!SH_OK(P, (long long)c < P.ncap, 3, c)) return;
       float o0, o1, o2, o3;
       up(oA, o0, o1);
       up(oB, o2, o3);
@@ -897,6 +950,7 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, i
 #pragma unroll 4
           for (int k = 0; k < 8; ++k, c += sb4) {
             const int row = r0 + 4 * k;
+            if (!SH_OK(P, (long long)c < P.ncap, 3, c)) continue;
             *reinterpret_cast<float4*>(P.qout + 4 * (size_t)c) =
                 *reinterpret_cast<const float4*>(ring + row * XQSTR + pc * 4);
             P.rout[c] = ring[XQ + row * XRSTR + pc];
@@ -908,6 +962,7 @@ __device__ __forceinline__ void sweep_item(const SweepParams& P, const Geo& G, i
             const long long tr = g * LANES + row;
             if (tr < G.plane()) {
               const unsigned c = (unsigned)G.off() + (unsigned)tr * (unsigned)G.sb() + (unsigned)pos;
+              if (!SH_OK(P, (long long)c < P.ncap, 3, c)) continue;
               *reinterpret_cast<float4*>(P.qout + 4 * (size_t)c) =
                   *reinterpret_cast<const float4*>(ring + row * XQSTR + pc * 4);
               P.rout[c] = ring[XQ + row * XRSTR + pc];
@@ -1008,6 +1063,7 @@ __device__ __forceinline__ void sweep_items(const SweepParams& P, const BatchLis
     for (int r = first; r < nranges; r += nwarps) {
       int x, end;
       if (P.ranges) {
+        if (!SH_OK(P, r + 1 <= P.nranges, 5, r)) break;
         x = P.ranges[r];
         end = P.ranges[r + 1];
       } else {

@@ -17,7 +17,9 @@ import threading
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libshasta.so")
+# SHASTA_LIBRARY may name another build of the library, e.g. the checked one
+# (build.build(checked=True)); there is no fallback if it is missing
+LIB_PATH = os.environ.get("SHASTA_LIBRARY") or os.path.join(HERE, "libshasta.so")
 
 OK, EINVAL, ENOMEM, EAGAIN, EUNPHYSICAL, ETIMEOUT, ECUDA, ENOTFOUND = range(8)
 BC_REFLECT, BC_PERIODIC, BC_FROZEN = 0, 1, 2
@@ -108,6 +110,7 @@ SIGNATURES = {
     "shasta_steps_done": (C.c_int64, [_vp]),
     "shasta_set_step_counter": (C.c_int, [_vp, C.c_int64]),
     "shasta_counters": (C.c_int, [_vp, C.POINTER(C.c_int64)]),
+    "shasta_checked_report": (C.c_int, [_vp, C.POINTER(C.c_ulonglong)]),
     "shasta_stream": (_vp, [_vp]),
     "shasta_last_error": (C.c_char_p, [_vp]),
     "shasta_status_string": (C.c_char_p, [C.c_int]),
@@ -128,6 +131,7 @@ SIGNATURES = {
     "shasta_batch_steps_done": (C.c_int64, [_vp, C.c_int]),
     "shasta_batch_set_step_counter": (C.c_int, [_vp, C.c_int, C.c_int64]),
     "shasta_batch_counters": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int64)]),
+    "shasta_batch_checked_report": (C.c_int, [_vp, C.POINTER(C.c_ulonglong)]),
     "shasta_batch_info": (C.c_int, [_vp, C.POINTER(C.c_int64)]),
     "shasta_batch_stream": (_vp, [_vp]),
     "shasta_batch_last_error": (C.c_char_p, [_vp]),
@@ -370,6 +374,12 @@ class Solver:
         _check(lib().shasta_counters(self._h, out), self._h)
         return int(out[0])
 
+    def checked_report(self):
+        """Checked builds: (refused accesses, first code, first index); clears."""
+        out = (C.c_ulonglong * 3)()
+        _check(lib().shasta_checked_report(self._h, out), self._h)
+        return tuple(int(x) for x in out)
+
     @property
     def stream(self):
         return lib().shasta_stream(self._h)
@@ -489,6 +499,12 @@ class Batch:
         out = (C.c_int64 * 1)()
         _bcheck(lib().shasta_batch_counters(self._h, eid, out), self._h)
         return int(out[0])
+
+    def checked_report(self):
+        """Checked builds: (refused accesses, first code, first index); clears."""
+        out = (C.c_ulonglong * 3)()
+        _bcheck(lib().shasta_batch_checked_report(self._h, out), self._h)
+        return tuple(int(x) for x in out)
 
     def info(self):
         out = (C.c_int64 * 7)()
