@@ -309,9 +309,10 @@ shasta_status shasta_set_step_counter(shasta_ctx* ctx, int64_t steps);
 shasta_status shasta_counters(shasta_ctx* ctx, int64_t out[1]);
 
 /* Checked builds only (the library built with SHASTA_CHECKED, a test aid
- * with no counterpart in the paper): the FP32 / MIXED sweep kernels test
- * every global and shared-memory access at a computed index against the
- * bounds of its buffer and skip it if it falls outside; out[0] = accesses
+ * with no counterpart in the paper): the sweep kernels test every global
+ * access (and the FP32 / MIXED ones every shared-memory access) at a
+ * computed index against the bounds of its buffer and skip it if it falls
+ * outside; out[0] = accesses
  * refused since the last report, out[1] / out[2] = code (1 state load,
  * 2 frozen-ghost load, 3 state store, 4 shared-memory ring, 5 range table)
  * and index of the first.  Clears the record.  Synchronous.  Errors: EINVAL

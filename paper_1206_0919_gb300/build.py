@@ -21,9 +21,10 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libshasta.so")
-# checked build: the same library with every global and shared-memory access
-# of the FP32 / MIXED sweeps bounds-tested (refused accesses are counted and
-# skipped; shasta_checked_report reads the record); for tests, not for speed
+# checked build: the same library with every global access of the sweeps and
+# every shared-memory access of the FP32 / MIXED ones bounds-tested (refused
+# accesses are counted and skipped; shasta_checked_report reads the record);
+# for tests, not for speed
 BUILD_CHECKED = os.path.join(HERE, "_build_checked")
 LIB_CHECKED = os.path.join(HERE, "libshasta_checked.so")
 

@@ -105,6 +105,27 @@ inline void set_float_scalars(SweepParams& P) {
   P.f_bag_ec = (float)P.bag_ec;
 }
 
+// Checked builds (-DSHASTA_CHECKED): each global access of the streaming
+// sweeps (FP64 and FP32 / MIXED), and each shared-memory access of the fast
+// sweeps at a computed offset, is first tested against the bounds of its
+// buffer; a miss is counted in P.chk (count, first code, first index) and
+// the access is skipped.  The tests run them to
+// show that the index arithmetic stays in bounds; other builds compile the
+// tests away.  Codes: 1 state load, 2 frozen-ghost load, 3 state store,
+// 4 shared-memory ring, 5 range table.
+#ifdef SHASTA_CHECKED
+__device__ __forceinline__ bool chk_ok(unsigned long long* rec, bool ok, int code, long long idx) {
+  if (!ok && rec && atomicAdd(rec, 1ull) == 0ull) {
+    rec[1] = (unsigned long long)code;
+    rec[2] = (unsigned long long)idx;
+  }
+  return ok;
+}
+#define SH_OK(P, cond, code, idx) ::shasta::chk_ok((P).chk, (cond), (code), (long long)(idx))
+#else
+#define SH_OK(P, cond, code, idx) true
+#endif
+
 // Batched sweeps: one event of a batch.  All events of a batch share the
 // batch's state arrays (qin/rin/qout/rout of SweepParams); the event's cells
 // are [off, off + nx*ny*nz) of each, x fastest.
@@ -295,6 +316,12 @@ __device__ __forceinline__ void load_ext(const SweepParams& P, long long base, l
   const int n = P.n;
   if (q >= 0 && q < n) {
     long long i = base + (long long)q * P.stride;
+#ifdef SHASTA_CHECKED
+    if (!SH_OK(P, i >= 0 && i < P.ncap, 1, i)) {
+      for (int k = 0; k < NF; ++k) v[k] = T(0);
+      return;
+    }
+#endif
     v[0] = ldv<T>(P.in[0], i);
     v[1] = ldv<T>(P.in[FPAR], i);
     v[2] = ldv<T>(P.in[FT1], i);
@@ -307,6 +334,12 @@ __device__ __forceinline__ void load_ext(const SweepParams& P, long long base, l
     int layer = q < 0 ? -1 - q : q - n;
     layer = layer > NG - 1 ? NG - 1 : layer;
     long long o = ((long long)(side * NG + layer) * NF) * P.plane + t;
+#ifdef SHASTA_CHECKED
+    if (!SH_OK(P, o >= 0 && t < P.plane && o + 4 * P.plane < 2LL * NG * NF * P.plane, 2, o)) {
+      for (int k = 0; k < NF; ++k) v[k] = T(0);
+      return;
+    }
+#endif
     v[0] = ldv<T>(P.frozen, o + 0 * P.plane);
     v[1] = ldv<T>(P.frozen, o + (long long)FPAR * P.plane);
     v[2] = ldv<T>(P.frozen, o + (long long)FT1 * P.plane);
@@ -325,6 +358,12 @@ __device__ __forceinline__ void load_ext(const SweepParams& P, long long base, l
     neg = m >= n;
   }
   long long i = base + (long long)src * P.stride;
+#ifdef SHASTA_CHECKED
+  if (!SH_OK(P, i >= 0 && i < P.ncap, 1, i)) {
+    for (int k = 0; k < NF; ++k) v[k] = T(0);
+    return;
+  }
+#endif
   v[0] = ldv<T>(P.in[0], i);
   T par = ldv<T>(P.in[FPAR], i);
   v[1] = neg ? -par : par;
@@ -478,7 +517,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(SweepParams P) {
       af[k] = an;
     }
     const int jo = q - 2 * NG;
-    if (jo >= s0) {
+    if (jo >= s0 && SH_OK(P, base + (long long)jo * P.stride < P.ncap, 3, base + (long long)jo * P.stride)) {
       long long i = base + (long long)jo * P.stride;
       static_cast<T*>(P.out[0])[i] = outv[0];
       static_cast<T*>(P.out[FPAR])[i] = outv[1];

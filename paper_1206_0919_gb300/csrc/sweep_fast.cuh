@@ -56,25 +56,6 @@
 namespace shasta {
 namespace fast {
 
-// Checked builds (-DSHASTA_CHECKED): each global access of the streaming
-// sweeps, and each shared-memory access at a computed offset, is first
-// tested against the bounds of its buffer; a miss is counted in P.chk (count,
-// first code, first index) and the access is skipped.  The tests run them to
-// show that the index arithmetic stays in bounds; other builds compile the
-// tests away.  Codes: 1 state load, 2 frozen-ghost load, 3 state store,
-// 4 shared-memory ring, 5 range table.
-#ifdef SHASTA_CHECKED
-__device__ __forceinline__ bool chk_ok(unsigned long long* rec, bool ok, int code, long long idx) {
-  if (!ok && rec && atomicAdd(rec, 1ull) == 0ull) {
-    rec[1] = (unsigned long long)code;
-    rec[2] = (unsigned long long)idx;
-  }
-  return ok;
-}
-#define SH_OK(P, cond, code, idx) ::shasta::fast::chk_ok((P).chk, (cond), (code), (long long)(idx))
-#else
-#define SH_OK(P, cond, code, idx) true
-#endif
 
 constexpr int LANES = 32;
 constexpr int CH = 8;      // x sweep: positions per cooperative chunk

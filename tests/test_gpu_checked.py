@@ -1,12 +1,13 @@
-"""The FP32 / MIXED sweep kernels stay inside their buffers.
+"""The sweep kernels stay inside their buffers.
 
 compute-sanitizer is not available to these tests, so the library is built a
 second time with SHASTA_CHECKED: every global access of the streaming sweeps
-(state loads and stores, frozen-ghost loads, the range table) and every
-shared-memory ring access at a computed offset is tested against its buffer's
-bounds first, and a miss is counted and skipped.  A child process runs the
-checked library over ragged shapes, every boundary rule, both closed-form
-EoS, single contexts under every launch choice (autotuned, uniform and
+(state loads and stores, frozen-ghost loads, the range table; FP64, FP32 and
+MIXED) and every shared-memory ring access of the FP32 / MIXED sweeps at a
+computed offset is tested against its buffer's bounds first, and a miss is
+counted and skipped.  A child process runs the checked library over ragged
+shapes, every boundary rule, both closed-form EoS, single contexts under
+every launch choice (autotuned, uniform and
 forced work ranges, both register variants, CTA work shares) and batches of
 uneven events (work units of whole line groups and of position ranges); it
 must report no refused access, and its states must be bitwise those of the
@@ -53,7 +54,7 @@ out = {}
 def report(obj):
     return list(obj.checked_report()) if checked else [0, 0, 0]
 
-for prec in ("fp32", "mixed"):
+for prec in ("fp32", "mixed", "fp64"):
     for si, shape in enumerate(SHAPES):
         for bc in ("reflect", "periodic", "frozen"):
             for eos in ("ideal", "bag"):
