@@ -173,6 +173,8 @@ def test_null_handles_are_rejected(lib):
     assert lib.shasta_steps_done(null) == -1
     assert lib.shasta_set_step_counter(null, 0) == S.EINVAL
     assert lib.shasta_counters(null, i64) == S.EINVAL
+    u64 = (C.c_ulonglong * 3)()
+    assert lib.shasta_checked_report(null, u64) == S.EINVAL
     assert lib.shasta_stream(null) is None
     assert lib.shasta_create(None, 1.0, 0.4, None, None, None) == S.EINVAL
     # batches
@@ -188,6 +190,7 @@ def test_null_handles_are_rejected(lib):
     assert lib.shasta_batch_totals(null, 0, dbl) == S.EINVAL
     assert lib.shasta_batch_steps_done(null, 0) == -1
     assert lib.shasta_batch_counters(null, 0, i64) == S.EINVAL
+    assert lib.shasta_batch_checked_report(null, u64) == S.EINVAL
     assert lib.shasta_batch_info(null, i64) == S.EINVAL
     assert lib.shasta_batch_stream(null) is None
     assert lib.shasta_batch_last_error(null) is not None
